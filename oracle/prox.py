@@ -1,0 +1,83 @@
+"""Per-cell proximal map of tau*phi, phi_{ij} = b_hat + F (Sec. 3).
+
+The paper takes the formula from its reference [BAKS, Cor. 3.1] without
+printing it; the oracle derives it from the first-order conditions for q' = 2:
+
+  phi(m, w) = |w|^2/(2m) + F_eff(m),  m > 0, w in K;  phi(0, 0) = F_eff(0),
+  F_eff(m) = F(x, m) [+ G(x, m)/dt on the last time plane, Sec. 2 calF].
+
+For fixed m > 0 the w-part is separable per component and the minimiser is
+w = m/(m + tau) * P with P = P_K(w_bar) (Sec. 2 projection onto K).  The
+envelope theorem then gives the scalar equation for m,
+
+  h(m) = m - m_bar + tau f_eff(m) - tau |P|^2 / (2 (m + tau)^2) = 0,
+
+with h strictly increasing because f_eff is nondecreasing.  If h(0) >= 0 the
+prox is (0, 0); otherwise the root lies in (0, m_hi] with
+m_hi = max(0, m_bar - tau f_eff(0)) + |P|^2/(2 tau), where h(m_hi) >= 0.
+The oracle brackets the root there and bisects until the bracket cannot shrink
+in FP64.  Pins: closed forms for P = 0, the zero branch, and brute-force
+minimisation of the definition on random cells (tests).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .operators import dt
+
+
+def project_K(wbar):
+    """P_K: components (1, 3) clipped to [0, inf), components (2, 4) to (-inf, 0]."""
+    P = np.array(wbar, dtype=np.float64, copy=True)
+    P[0::2] = np.maximum(P[0::2], 0.0)
+    P[1::2] = np.minimum(P[1::2], 0.0)
+    return P
+
+
+def coupling(prob, V, W):
+    """Per-plane coefficients of f_eff(m) = a m + b m^2 + c: (a, b, c) with
+    a, c of shape (nt, Nx, Ny); the last plane carries g/dt (Sec. 2, calF)."""
+    nt = prob["nt"]
+    nx, ny = prob["n"]
+    a = np.full((nt, nx, ny), prob["f_a"])
+    c = np.broadcast_to(np.asarray(V, dtype=np.float64).reshape(nx, ny), (nt, nx, ny)).copy()
+    a[-1] += prob["g_a"] / dt(prob)
+    c[-1] += np.asarray(W, dtype=np.float64).reshape(nx, ny) / dt(prob)
+    return a, prob["f_b"], c
+
+
+def h_eq(m, mbar, P2, tau, a, b, c):
+    return m - mbar + tau * (a * m + b * m * m + c) - tau * P2 / (2.0 * (m + tau) ** 2)
+
+
+def prox(prob, tau, v, V, W, max_iter=4000):
+    """prox_{tau phi}(v) for v of shape (c, nt, Nx, Ny); returns the same shape."""
+    v = np.asarray(v, dtype=np.float64)
+    mbar = v[0]
+    P = project_K(v[1:])
+    P2 = (P * P).sum(axis=0)
+    a, b, c = coupling(prob, V, W)
+    zero = h_eq(0.0, mbar, P2, tau, a, b, c) >= 0.0
+    lo = np.zeros_like(mbar)
+    hi = np.maximum(0.0, mbar - tau * c) + P2 / (2.0 * tau)
+    active = ~zero
+    for _ in range(max_iter):
+        if not active.any():
+            break
+        mid = lo + 0.5 * (hi - lo)
+        stuck = (mid <= lo) | (mid >= hi)
+        active &= ~stuck
+        hm = h_eq(mid, mbar, P2, tau, a, b, c)
+        neg = active & (hm < 0.0)
+        pos = active & ~(hm < 0.0)
+        lo = np.where(neg, mid, lo)
+        hi = np.where(pos, mid, hi)
+    hlo = np.abs(h_eq(lo, mbar, P2, tau, a, b, c))
+    hhi = np.abs(h_eq(hi, mbar, P2, tau, a, b, c))
+    m = np.where(hlo < hhi, lo, hi)
+    m = np.where(zero, 0.0, m)
+    out = np.empty_like(v)
+    out[0] = m
+    out[1:] = (m / (m + tau))[None] * P
+    out[1:, zero] = 0.0
+    return out

@@ -1,0 +1,170 @@
+"""Linear solvers for the oracle: direct LU, plain CG, and the exact
+spatially-diagonalised solver.
+
+The spatially-diagonalised solver follows Sec. 4.3: K = F^{-1} Lambda F with F a
+DFT (periodic axis) or an orthonormal DCT-II (Neumann axis), eigenvalues
+2 - 2cos(2 pi v/N)/dx^2 and 2 - 2cos(pi v/N)/dx^2 (Alg. 2), and B B^T = 2K
+(eq. precstead).  Every block of AAt (eq. largeA) and of P (eq. prec) is then a
+polynomial in K, so in K's eigenbasis each spatial mode leaves one symmetric
+tridiagonal N_t x N_t system, solved here by Thomas elimination.  This is an
+exact direct method, not the paper's preconditioned CG; it is pinned against
+sparse LU on small grids.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.fft as sfft
+import scipy.sparse.linalg as spla
+
+from .operators import PERIODIC, dt, spacing
+
+
+def solve_direct(A, b):
+    """Sparse LU solve (SuperLU through scipy)."""
+    return spla.splu(A.tocsc()).solve(np.asarray(b, dtype=np.float64))
+
+
+def solve_cg(A, b, tol=1e-12, x0=None, maxiter=100000):
+    """Unpreconditioned conjugate gradients (Hestenes-Stiefel), stopping when
+    ||b - A x||_2 <= tol ||b||_2.  Returns (x, iterations)."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b - A @ x
+    p = r.copy()
+    rr = r @ r
+    bn = np.sqrt(b @ b)
+    it = 0
+    while np.sqrt(rr) > tol * bn and it < maxiter:
+        q = A @ p
+        alpha = rr / (p @ q)
+        x += alpha * p
+        r -= alpha * q
+        rr_new = r @ r
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    return x, it
+
+
+def laplacian_eigs(prob):
+    """Eigenvalues kappa_s of K on the (Nx, Ny) mode grid, in the order of the
+    transforms used by `to_modes` (Alg. 2, lines 1-8)."""
+    out = []
+    dims = 2 if prob["dim"] == 2 else 1
+    for ax in range(dims):
+        n = prob["n"][ax]
+        h = spacing(prob)[ax]
+        v = np.arange(n)
+        if prob["bc"][ax] == PERIODIC:
+            lam = 2.0 - 2.0 * np.cos(2.0 * np.pi * v / n)
+        else:
+            lam = 2.0 - 2.0 * np.cos(np.pi * v / n)
+        out.append(lam / h ** 2)
+    if dims == 1:
+        return out[0][:, None]
+    return out[0][:, None] + out[1][None, :]
+
+
+def to_modes(prob, u):
+    """Forward spatial transform of a (nt, Nx, Ny) array: DFT on periodic axes,
+    orthonormal DCT-II on Neumann axes."""
+    u = np.asarray(u)
+    axes = [1, 2] if prob["dim"] == 2 else [1]
+    for a in axes:
+        if prob["bc"][a - 1] == PERIODIC:
+            u = np.fft.fft(u, axis=a)
+        else:
+            u = sfft.dct(u, type=2, norm="ortho", axis=a)
+    return u
+
+
+def from_modes(prob, u):
+    axes = [2, 1] if prob["dim"] == 2 else [1]
+    for a in axes:
+        if prob["bc"][a - 1] == PERIODIC:
+            u = np.fft.ifft(u, axis=a)
+        else:
+            if np.iscomplexobj(u):
+                u = sfft.idct(u.real, type=2, norm="ortho", axis=a) + \
+                    1j * sfft.idct(u.imag, type=2, norm="ortho", axis=a)
+            else:
+                u = sfft.idct(u, type=2, norm="ortho", axis=a)
+    return u
+
+
+def thomas(diag, off, rhs):
+    """Symmetric tridiagonal solve along axis 0 for every column at once.
+    diag: (nt, ...), off: (...) constant off-diagonal, rhs: (nt, ...)."""
+    nt = diag.shape[0]
+    c = np.empty(diag.shape, dtype=np.result_type(diag, off))
+    d = np.empty(rhs.shape, dtype=np.result_type(rhs, diag, off))
+    c[0] = off / diag[0]
+    d[0] = rhs[0] / diag[0]
+    for k in range(1, nt):
+        den = diag[k] - off * c[k - 1]
+        c[k] = off / den
+        d[k] = (rhs[k] - off * d[k - 1]) / den
+    x = np.empty_like(d)
+    x[nt - 1] = d[nt - 1]
+    for k in range(nt - 2, -1, -1):
+        x[k] = d[k] - c[k] * x[k + 1]
+    return x
+
+
+def _shape(prob):
+    nx, ny = prob["n"]
+    return prob["nt"], nx, ny
+
+
+def solve_AAt_modal(prob, b):
+    """Exact solve of AAt z = b.  Per spatial mode s with eigenvalue kappa:
+    L_s = nu kappa + 1/dt, C_s = L_s^2 + 2 kappa; diagonal (C_s, C_s + 1/dt^2, ...),
+    off-diagonal -L_s/dt (eq. largeA with B B^T = 2K)."""
+    nt, nx, ny = _shape(prob)
+    kap = laplacian_eigs(prob)
+    h = dt(prob)
+    Ls = prob["nu"] * kap + 1.0 / h
+    Cs = Ls ** 2 + 2.0 * kap
+    diag = np.broadcast_to(Cs, (nt,) + Cs.shape).copy()
+    diag[1:] += 1.0 / h ** 2
+    bh = to_modes(prob, np.asarray(b, dtype=np.float64).reshape(nt, nx, ny))
+    zh = thomas(diag, -Ls / h, bh)
+    return np.real(from_modes(prob, zh)).reshape(-1)
+
+
+def precond_modal(prob, r):
+    """Exact P^{-1} r for eq. prec: per spatial mode, C_hat_s = nu^2 kappa^2 + 2 kappa,
+    L_hat_s = (nu kappa + 1/dt)/dt, diagonal (C_hat + l L_hat, C_hat + 2 L_hat, ...),
+    off-diagonal -L_hat (no time transform involved)."""
+    nt, nx, ny = _shape(prob)
+    kap = laplacian_eigs(prob)
+    h = dt(prob)
+    Lh = (prob["nu"] * kap + 1.0 / h) / h
+    Ch = prob["nu"] ** 2 * kap ** 2 + 2.0 * kap
+    diag = np.broadcast_to(Ch + 2.0 * Lh, (nt,) + Ch.shape).copy()
+    diag[0] = Ch + prob["l"] * Lh
+    rh = to_modes(prob, np.asarray(r, dtype=np.float64).reshape(nt, nx, ny))
+    zh = thomas(diag, -Lh, rh)
+    return np.real(from_modes(prob, zh)).reshape(-1)
+
+
+def pcg(apply_A, apply_Minv, b, tol, x0=None, maxiter=10000):
+    """Preconditioned CG (Fletcher-Reeves beta), ||r|| <= tol ||b||; returns (x, it)."""
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - apply_A(x)
+    z = apply_Minv(r)
+    p = z.copy()
+    rz = r @ z
+    bn = np.sqrt(b @ b)
+    it = 0
+    while np.sqrt(r @ r) > tol * bn and it < maxiter:
+        q = apply_A(p)
+        alpha = rz / (p @ q)
+        x += alpha * p
+        r -= alpha * q
+        z = apply_Minv(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        it += 1
+    return x, it
