@@ -1,0 +1,417 @@
+"""Throughput benchmark of the GB300 variational-MFG solver.
+
+Workload: 2-D periodic torus 128 x 128, N_t = 64 (n = 1,048,576 space-time
+unknowns, 5n primal unknowns), quadratic Hamiltonian, f = m + V(x) with V a
+seeded sum of 8 Fourier modes, g = 0, m0 a seeded 3-Gaussian mixture, solved
+for the four viscosities nu in {1e-3, 1e-2, 1e-1, 1} as one batched plan.
+
+One step = one fixed-count solve: 300 accelerated Chambolle-Pock iterations
+(each with its preconditioned AAt solve to relative tolerance 1e-10 and the
+per-cell prox) on each of the four instances, started from the initial
+iterate; the four instances run as parallel branches of one CUDA graph launch.
+Metric: CP iterations per second, summed over instances (each CP iteration is
+one preconditioned AAt solve).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+benchmark) on a bounded sample of the same workload.  Under torchrun each rank
+solves its own copy of the batch (replicas; no data-path collective) and rank 0
+prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+import mfg_inputs as mi
+
+NUS = mi.CONFIG2_NU
+CP_PER_STEP = 300
+CG_TOL = 1e-10
+METRIC = "CP iterations/s (preconditioned AAt solves/s), 2-D periodic 128^2 x 64, 4 viscosities"
+WORKLOAD = "2-D periodic torus 128x128, N_t=64, nu in {1e-3,1e-2,1e-1,1}, 300 CP iterations per instance per step"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value, world, backend_device=None):
+    """Max of a float over ranks (identity for a single process)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([value], dtype=torch.float64, device=backend_device or "cpu")
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value, world, backend_device=None):
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([value], dtype=torch.float64, device=backend_device or "cpu")
+    td.all_reduce(t, op=td.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 flops of one AAt apply per unknown in the fused factored form: K p
+# (4 differences, 2 adds, 2 scalings, 1 add = 9), xm = nu Kp + (p - p')/dt (4),
+# q = nu K xm + (xm - xm')/dt + 2 Kp (10 + 2 + 2) -> 27.
+AAT_FLOPS_PER_UNKNOWN = 27
+# GB300 FP64 rate (recipe table: 1.25 TFLOP/s); an FMA-chain probe on this machine
+# measured 1.196 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def build_batch(precision, cp_per_step=CP_PER_STEP):
+    insts = [mi.config2(nu=nu) for nu in NUS]
+    probs = []
+    for inst in insts:
+        p = dict(inst["problem"], max_cp=cp_per_step, cg_tol=CG_TOL, precision=precision)
+        probs.append(p)
+    return insts, probs
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl", device_id=dev)
+    import paper_2507_01958_gb300 as pkg
+    L = pkg.lib()
+    insts, probs = build_batch(args.precision, args.cp_per_step)
+    plan = L.mfg_plan(probs)
+    if args.eager:
+        L.mfg_set_launch_mode(plan, "eager")
+    sz = L.mfg_sizes(plan)
+    cat = lambda key: np.concatenate([np.asarray(i[key], dtype=np.float64).reshape(-1) for i in insts])
+    m0_h, V_h, W_h, y0_h = cat("m0"), cat("V"), cat("W"), cat("y0")
+    m0 = torch.as_tensor(m0_h, device=dev)
+    V = torch.as_tensor(V_h, device=dev)
+    W = torch.as_tensor(W_h, device=dev)
+    y0 = torch.as_tensor(y0_h, device=dev)
+    y, ybar = torch.empty_like(y0), torch.empty_like(y0)
+    z = torch.zeros(sz["dual"], dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        y.copy_(y0)
+        ybar.copy_(y0)
+        z.zero_()
+        rc, st = L.mfg_solve(plan, m0, V, W, y, ybar, z, stream=stream)
+        if rc != 0:
+            raise RuntimeError(f"solve failed: {rc} {L.mfg_last_error()}")
+        return st
+
+    for _ in range(args.warmup):
+        st = step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as td
+        td.barrier()
+    l0 = L.mfg_kernel_launches(plan)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    cg_total = 0
+    cp_total = 0
+    for _ in range(args.steps):
+        st = step()
+        cg_total += sum(s.cg_iters for s in st)
+        cp_total += sum(s.cp_iters for s in st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = L.mfg_kernel_launches(plan) - l0
+    t_local = e0.elapsed_time(e1) / 1e3
+    t = reduce_max(t_local, world, dev)
+    cp_all = reduce_sum(float(cp_total), world, dev)
+    cg_all = reduce_sum(float(cg_total), world, dev)
+    n_per = probs[0]["nt"] * probs[0]["n"][0] * probs[0]["n"][1]
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "value": cp_all / t, "unit": "CP iterations/s",
+                              "ms_per_step": 1e3 * t / max(args.steps, 1), "pcg_iters": cg_all,
+                              "cp_iters": cp_all, "gpu_launches": int(launches)}))
+        return
+
+    # FP64 reference path of the same workload: one step, for the mixed-vs-FP64 ratio.
+    _, probs64 = build_batch("fp64", args.cp_per_step)
+    plan64 = L.mfg_plan(probs64)
+    y64, ybar64 = torch.empty_like(y0), torch.empty_like(y0)
+    z64 = torch.zeros_like(z)
+
+    def step64():
+        y64.copy_(y0)
+        ybar64.copy_(y0)
+        z64.zero_()
+        rc, st = L.mfg_solve(plan64, m0, V, W, y64, ybar64, z64, stream=stream)
+        return st
+
+    step64()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    st64 = step64()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    t64 = f0.elapsed_time(f1) / 1e3
+    cp64 = sum(s.cp_iters for s in st64)
+    # accuracy of the mixed iterate against the FP64 GPU path (same inputs, same count)
+    step()
+    torch.cuda.synchronize()
+    err_mixed = float(torch.linalg.norm(y - y64) / torch.linalg.norm(y64))
+
+    # Dominant-kernel roofline: the fused AAt stencil, timed with CUDA events on
+    # the stream it is launched on, same launch shape as inside the solve graph.
+    p_in = torch.randn(n_per, dtype=torch.float64, device=dev)
+    q_out = torch.empty_like(p_in)
+    for _ in range(3):
+        L.mfg_apply_AAt(plan, 0, p_in, q_out, stream=stream)
+    reps = 50
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(reps):
+        L.mfg_apply_AAt(plan, 0, p_in, q_out, stream=stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    t_aat = a0.elapsed_time(a1) / 1e3 / reps
+    flops = AAT_FLOPS_PER_UNKNOWN * n_per
+    achieved = flops / t_aat / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "k_AAt_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get("bytes_per_launch")
+
+    # End to end through the host-buffer entry point (copies inside the timed region).
+    pin = lambda a: torch.as_tensor(a).pin_memory()
+    hm0, hV, hW = pin(m0_h), pin(V_h), pin(W_h)
+    hy, hyb = pin(y0_h.copy()), pin(y0_h.copy())
+    hz = torch.zeros(sz["dual"], dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hy.copy_(torch.from_numpy(y0_h))
+        hyb.copy_(torch.from_numpy(y0_h))
+        hz.zero_()
+        rc, st = L.mfg_solve_host(plan, hm0, hV, hW, hy, hyb, hz, stream=stream)
+    h1 = time.perf_counter()
+    t_e2e = reduce_max(h1 - h0, world, dev)
+    cp_e2e = reduce_sum(float(sum(s.cp_iters for s in st) * e2e_steps), world, dev)
+    h2d = 8 * (3 * sz["field"] + 2 * sz["primal"] + sz["dual"])
+    d2h = 8 * (2 * sz["primal"] + sz["dual"])
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(args.cpu_seconds)
+
+    peaks, src = load_peaks()
+    if rank == 0:
+        out = {
+            "metric": METRIC,
+            "value": cp_all / t,
+            "unit": "CP iterations/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64+f32",
+            "data": "synthetic (seeded fields shaped like the paper's experiments)",
+            "config": {"workload": WORKLOAD, "instances": len(NUS), "unknowns_per_instance": n_per,
+                       "primal_unknowns_per_instance": 5 * n_per, "pcg_rel_tol": CG_TOL,
+                       "precision": "mixed", "parallelism": f"replicas x{world}",
+                       "l2": "working set 4 x ~128 MB > 129 MB L2; no flush"},
+            "pcg_iters_per_s": cg_all / t,
+            "unknowns_cp_iters_per_s": cp_all * n_per / t,
+            "avg_pcg_per_cp": cg_all / max(cp_all, 1.0),
+            "fp64_path": {"value": cp64 / t64, "unit": "CP iterations/s", "ms_per_step": 1e3 * t64},
+            "mixed_vs_fp64_speedup": (cp_all / t) / (cp64 / t64) / world,
+            "mixed_rel_err_vs_fp64_path": err_mixed,
+            "roofline": {"kernel": "k_AAt (fused C C^T stencil, FP64)", "bound": "alu",
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                         "algorithmic_flops_per_launch": flops, "avg_launch_us": 1e6 * t_aat,
+                         "hbm_achieved_gbs": 16 * n_per / t_aat / 1e9,
+                         "hbm_peak_gbs": peaks.get("hbm_gbs"), "peak_source": src},
+            "cpu_baseline": cpu,
+            "e2e": {"value": cp_e2e / t_e2e, "unit": "CP iterations/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as td
+        td.barrier()
+        td.destroy_process_group()
+
+
+def cpu_baseline_sample(seconds=15.0, steps=None):
+    """The oracle, as it stands, on a bounded sample: CP iterations of the
+    nu = 1e-2 instance with its exact spatially-diagonalised solver."""
+    from oracle.cp import Solver
+    inst = mi.config2(nu=1e-2)
+    p = dict(inst["problem"])
+    s = Solver(p, inst["m0"], inst["V"], inst["W"], method="modal")
+    y = inst["y0"]
+    state = {}
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        res = s.run(y, iters=1, ybar0=state.get("ybar"), x0=state.get("x"), tau0=state.get("tau"),
+                    sigma0=state.get("sigma"))
+        y = res["y"]
+        state = {"ybar": res["ybar"], "x": res["x"], "tau": res["tau"], "sigma": res["sigma"]}
+        done += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and done >= steps) or (steps is None and el >= seconds):
+            break
+    return {"value": done / el, "unit": "CP iterations/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} CP iterations of the nu=1e-2 instance (oracle, exact modal AAt solve, "
+                      f"bisection prox), {el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline_sample(steps=1)
+    t0 = time.perf_counter()
+    res = cpu_baseline_sample(steps=args.steps)
+    t = time.perf_counter() - t0
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": res["value"],
+        "unit": "CP iterations/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded fields shaped like the paper's experiments)",
+        "config": {"workload": WORKLOAD, "instances": len(NUS), "sample": "one CP iteration per step"},
+        "cpu_baseline": {"value": res["value"], "unit": "CP iterations/s", "cores": 1, "kind": "oracle",
+                         "sample": res["sample"]},
+        "e2e": {"value": res["value"], "unit": "CP iterations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cp-per-step", type=int, default=CP_PER_STEP)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--quick", action="store_true", help="main timed loop only (profiling runs)")
+    ap.add_argument("--eager", action="store_true",
+                    help="issue kernels one by one instead of one graph launch (per-kernel profiling)")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

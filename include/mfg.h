@@ -1,0 +1,179 @@
+/*
+ * mfg.h - C ABI of the GB300 solver for time-dependent variational mean field
+ * games (Ljosheim, Kalise, Pearson, Silva: "Parallel-in-Time Preconditioning
+ * for Time-Dependent Variational Mean Field Games", arXiv 2507.01958).
+ *
+ * The library solves problem (VMFG_h) of Sec. 2 (periodic torus or Neumann
+ * rectangle, d = 1 or 2, quadratic Hamiltonian H = |p|^2/2) with the
+ * accelerated Chambolle-Pock iteration of Sec. 3 and Sec. 5.  Each iteration
+ * needs one solve with AAt = C C^T (eq. largeA), done by preconditioned CG with
+ * the parallel-in-time preconditioner P of Sec. 4 (eq. prec / eq. pstrec:
+ * time DCT-VIII (l = 1) or DST-I (l = 2), exact spatial diagonalisation per
+ * time frequency, Alg. 1 and Alg. 2), and one per-cell proximal map of phi.
+ *
+ * Conventions shared by every entry point
+ *   - All arrays are FP64 and live in DEVICE memory owned by the caller unless
+ *     the entry point says otherwise (mfg_solve_host).  The library never
+ *     frees or retains caller pointers past the call.
+ *   - Grid layout: a spatial field is [Nx][Ny] (j fastest); a space-time field
+ *     is [Nt][Nx][Ny], size n = Nt*Nx*Ny (Ny = 1 when dim = 1).  Plane k of a
+ *     space-time field holds time level k+1 for m and level k for w, i.e. cell
+ *     k pairs (m^{k+1}, w^k) as the scheme (MFG_T2h) of Sec. 2 does.
+ *   - The primal y = (m, w) is c = 1 + 2*dim consecutive space-time planes
+ *     (m, w1, w2[, w3, w4]); w1/w2 are the x-direction components of the
+ *     cone K = [0,inf) x (-inf,0] (x [0,inf) x (-inf,0]) of Sec. 2, w3/w4 the
+ *     y-direction ones.
+ *   - Batched plans hold several instances; their arrays are concatenated in
+ *     instance order at the offsets mfg_layout reports.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued on it; entry points that report results on the host
+ *     synchronise it before returning and say so.
+ *   - Every function returns MFG_OK or an error code; mfg_last_error gives the
+ *     text.  Nothing aborts or throws across this boundary.  A plan is not safe
+ *     for concurrent use from two threads or two streams.
+ */
+#ifndef MFG_H
+#define MFG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum mfg_status {
+  MFG_OK = 0,
+  MFG_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range          */
+  MFG_ERR_UNSUPPORTED = 2,   /* valid in the paper, not built here (e.g. q' != 2)     */
+  MFG_ERR_CUDA = 3,          /* a CUDA runtime call failed                            */
+  MFG_ERR_NOT_CONVERGED = 4, /* PCG hit max_cg before reaching its tolerance          */
+  MFG_ERR_NONFINITE = 5,     /* NaN or Inf appeared in a residual or step             */
+  MFG_ERR_TIMEOUT = 6        /* a bounded device-side wait ran out                    */
+};
+
+enum { MFG_PERIODIC = 0, MFG_NEUMANN = 1 };
+/* MFG_FP64: every step in FP64.  MFG_MIXED: the preconditioner (transforms and
+ * per-frequency division) in FP32 inside FP64 flexible PCG; AAt, residuals,
+ * dot products and the prox stay FP64. */
+enum { MFG_FP64 = 0, MFG_MIXED = 1 };
+/* PCG tolerance: fixed cg_tol, or the paper's rule
+ * min{1e-4, max{1e-6, 1e-4 r}} with r the last CP step (Sec. 5). */
+enum { MFG_CG_FIXED = 0, MFG_CG_ADAPTIVE = 1 };
+
+/* One instance of (VMFG_h).  Paper symbols in brackets. */
+typedef struct {
+  int dim;           /* spatial dimension d: 1 or 2 (Sec. 2)                         */
+  int n[2];          /* Nx, Ny grid points (Ny ignored, taken as 1, when dim = 1)    */
+  double len[2];     /* domain lengths b-a, d-c (Sec. 2)                              */
+  int bc[2];         /* MFG_PERIODIC | MFG_NEUMANN per axis (Alg. 2 allows mixed)    */
+  int nt;            /* N_t >= 2 time steps                                           */
+  double T;          /* horizon T > 0, dt = T/N_t                                      */
+  double nu;         /* viscosity nu >= 0                                              */
+  double qprime;     /* Hamiltonian exponent q' of eq. power_hamiltonian; only 2      */
+  double f_a, f_b;   /* f(x,m) = f_a m + f_b m^2 + V(x); f_a, f_b >= 0 (monotone f)   */
+  double g_a;        /* g(x,m) = g_a m + W(x); g_a >= 0                                */
+  int l;             /* time preconditioner: 1 = DCT-VIII, 2 = DST-I (Sec. 4.1)       */
+  double gamma;      /* acceleration constant gamma > 0 (Sec. 5)                       */
+  double tau0, sigma0; /* initial step sizes (Sec. 5: 1 and 1)                         */
+  int max_cp;        /* CP iterations per mfg_solve call                               */
+  double cp_tol;     /* stop when ||m_{l+1} - m_l||_2 <= cp_tol; <= 0 disables (Sec. 5) */
+  int cg_rule;       /* MFG_CG_FIXED | MFG_CG_ADAPTIVE                                 */
+  double cg_tol;     /* relative PCG tolerance for MFG_CG_FIXED                        */
+  int max_cg;        /* PCG iteration cap per solve                                    */
+  int precision;     /* MFG_FP64 | MFG_MIXED                                           */
+} mfg_problem;
+
+/* Per-instance run record.  On entry to mfg_solve, `ell`, `tau`, `sigma` are
+ * the resume state (ell = 0 starts from tau0, sigma0); on return all fields
+ * describe the state after the call. */
+typedef struct {
+  int status;          /* mfg_status of this instance                                 */
+  int ell;             /* CP iterations done in total (resume counter)                */
+  int cp_iters;        /* CP iterations done by this call                             */
+  int max_cg_in_solve; /* largest PCG count of one solve in this call                 */
+  long long cg_iters;  /* PCG iterations done by this call                            */
+  double r_last;       /* ||m_{l+1} - m_l||_2 of the last iteration                    */
+  double tau, sigma;   /* step sizes for the next iteration                            */
+} mfg_stats;
+
+typedef struct mfg_plan_s* mfg_plan_t;
+
+/* Validates `batch` problems, builds the eigenvalue tables (eq. eigs, Alg. 2
+ * lines 1-10) and transform matrices on the host in FP64, uploads them and
+ * allocates all device workspace on the current device.  Rejects q' != 2
+ * (MFG_ERR_UNSUPPORTED), N_t < 2, N < 2, T <= 0, nu < 0, f_a/f_b/g_a < 0,
+ * l not in {1,2}, N_t > 256 (UNSUPPORTED).  *out is NULL on failure. */
+int mfg_plan(const mfg_problem* probs, int batch, mfg_plan_t* out);
+
+/* Frees all plan-owned memory.  NULL is accepted. */
+int mfg_destroy(mfg_plan_t plan);
+
+/* Thread-local text of the last error raised in this thread ("" if none). */
+const char* mfg_last_error(void);
+
+/* Element offsets of instance b inside the concatenated batch arrays:
+ * field (m0, V, W: Nx*Ny each), primal (y, ybar: c*n each), dual (z: n), plus
+ * the instance sizes.  Any output pointer may be NULL. */
+int mfg_layout(mfg_plan_t plan, int b, size_t* field_off, size_t* primal_off,
+               size_t* dual_off, size_t* n, int* c);
+
+/* Totals of the concatenated batch arrays (elements). */
+int mfg_sizes(mfg_plan_t plan, size_t* field_total, size_t* primal_total,
+              size_t* dual_total);
+
+/* Runs up to max_cp accelerated Chambolle-Pock iterations (Sec. 3 eq.
+ * pasosChamPock, step sizes of Sec. 5) on every instance of the plan.
+ *   m0, V, W : fields [Nx][Ny] per instance (m0 = m^0, V and W of f and g)
+ *   y        : in/out primal (m, w); caller sets m^k = m0, w = 0 (or any start)
+ *   ybar     : in/out extrapolated primal; set ybar = y for a fresh start
+ *   z        : in/out dual multiplier with x = C^T z; set z = 0 for a fresh start
+ *   st       : array of `batch` records, in/out (resume state on entry)
+ * The dual x = prox_{sigma psi*}(...) of eq. CC* is never stored: the library
+ * keeps z and forms C^T z where needed.  The whole solve is one CUDA graph
+ * launch; the call synchronises `stream` and fills `st` before returning.
+ * Returns the first non-OK instance status, or MFG_OK. */
+int mfg_solve(mfg_plan_t plan, const double* m0, const double* V, const double* W,
+              double* y, double* ybar, double* z, mfg_stats* st, void* stream);
+
+/* Same as mfg_solve with HOST buffers: copies the inputs into plan-owned device
+ * buffers, solves, and copies y, ybar, z back.  Synchronous. */
+int mfg_solve_host(mfg_plan_t plan, const double* m0, const double* V,
+                   const double* W, double* y, double* ybar, double* z,
+                   mfg_stats* st, void* stream);
+
+/* z = P^{-1} r for instance b (Alg. 1 with Alg. 2 in place of line 6, eq.
+ * pstrec), in the plan's precision.  r, z: n elements; must not alias. */
+int mfg_apply_precond(mfg_plan_t plan, int b, const double* r, double* z, void* stream);
+
+/* y = prox_{tau phi}(v) for instance b, cell by cell (Sec. 3; phi_ij = b_hat +
+ * F, plus G/dt on the last plane).  v, y: c*n elements; y == v allowed.
+ * V, W: the instance's fields. */
+int mfg_prox(mfg_plan_t plan, int b, double tau, const double* v, const double* V,
+             const double* W, double* y, void* stream);
+
+/* q = C C^T p (eq. largeA) for instance b; p, q: n elements, no aliasing. */
+int mfg_apply_AAt(mfg_plan_t plan, int b, const double* p, double* q, void* stream);
+
+/* r = C v (eq. ABC, reduced: the m0 term excluded) for instance b; v: c*n, r: n. */
+int mfg_apply_C(mfg_plan_t plan, int b, const double* v, double* r, void* stream);
+
+/* x = C^T p for instance b; p: n, x: c*n. */
+int mfg_apply_Ct(mfg_plan_t plan, int b, const double* p, double* x, void* stream);
+
+/* Number of kernel launches the library enqueued since the plan was made
+ * (graph nodes executed by mfg_solve are counted per execution). */
+long long mfg_kernel_launches(mfg_plan_t plan);
+
+/* How mfg_solve issues its kernels.  MFG_LAUNCH_GRAPH (default): the whole
+ * solve is one CUDA graph launch with device-side loop control.
+ * MFG_LAUNCH_EAGER: the same kernels with the same launch shapes, issued one
+ * by one on `stream`, the host reading the convergence flags after every PCG
+ * iteration (slower; lets per-kernel profilers see each launch, which they
+ * cannot inside graphs with conditional nodes). */
+enum { MFG_LAUNCH_GRAPH = 0, MFG_LAUNCH_EAGER = 1 };
+int mfg_set_launch_mode(mfg_plan_t plan, int mode);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFG_H */

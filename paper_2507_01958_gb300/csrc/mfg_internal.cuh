@@ -1,0 +1,105 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+#include "../../include/mfg.h"
+
+namespace mfg {
+
+constexpr int kThreads = 256;        // threads per block for 1-D launches
+constexpr int kRedBlocks = 152 * 4;  // fixed grid of the grid-stride reduction kernels
+constexpr int kMaxNt = 256;          // largest N_t of the fused time-transform kernel
+
+// Geometry and coefficients of one instance on the device.  Internally every
+// instance is a 2-axis grid: a 1-D problem is stored as Nx_int = 1 (inactive x
+// axis) and Ny_int = N, so its two w planes are the y-axis components.
+struct Geom {
+  int nx, ny, nt;   // internal sizes
+  int S;            // nx*ny
+  long long n;      // nt*S
+  int perx, pery;   // 1 = periodic axis, 0 = Neumann
+  int actx;         // x axis carries terms (dim == 2)
+  int c;            // primal planes: 3 or 5
+  double ax, ay;    // 1/dx^2, 1/dy^2 (ax = 0 on an inactive axis)
+  double idx, idy;  // 1/dx, 1/dy
+  double idt;       // 1/dt
+  double nu;
+};
+
+// Coefficients of f_eff(m) = a m + b m^2 + c(x) (Sec. 2 calF).
+struct Coef {
+  double f_a, f_b, g_a;  // g enters the last plane divided by dt
+  double gamma;
+};
+
+// Per-instance scalar state in device memory, written by the last block of the
+// reduction kernels.  Keeping it on the device lets a whole solve run as one
+// graph launch with no host round trip.
+struct DevScalars {
+  // Chambolle-Pock
+  double tau, sigma, r_last, dm2;
+  double cg_tol;        // relative tolerance of the current solve
+  double cp_tol;
+  int ell, cp_left, cp_done, status;
+  long long cg_total;
+  int cg_max, cp_iters;
+  // PCG
+  double bnorm2, rz, pq, alpha, beta, rr, qz;
+  int cg_it, cg_done, max_cg, cg_rule;
+  double cg_tol_fixed;
+  unsigned int counter;  // last-block ticket
+  unsigned int pad;
+};
+
+// Grid-stride 1-D launch shape shared by reduction kernels.
+inline int red_blocks(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  return (int)(b < kRedBlocks ? (b > 0 ? b : 1) : kRedBlocks);
+}
+
+// ---------------------------------------------------------------- kernels --
+// Stencils (k_stencil.cu).
+void launch_apply_C(const Geom& g, const double* v, double* r, double alpha, const double* m0,
+                    double* partials, DevScalars* sc, int mode, cudaStream_t s);
+void launch_apply_Ct(const Geom& g, const double* p, double* x, cudaStream_t s);
+void launch_AAt(const Geom& g, const double* p, double* q, double* partials, DevScalars* sc,
+                int mode, cudaStream_t s);
+int aat_blocks(const Geom& g);
+
+// Vector kernels (k_cg.cu).
+void launch_init_p(long long n, const double* zp, double* p, const double* r, double* partials,
+                   DevScalars* sc, cudaStream_t s);
+void launch_update_zr(long long n, double* z, double* r, const double* p, const double* q,
+                      double* partials, DevScalars* sc, cudaStream_t s);
+void launch_dot_beta(long long n, const double* r, const double* zp, const double* q, int flexible,
+                     double* partials, DevScalars* sc, cudaStream_t s);
+void launch_update_p(long long n, const double* zp, double* p, DevScalars* sc,
+                     cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
+void launch_scalars_begin(DevScalars* sc, cudaGraphConditionalHandle h, int use_handle,
+                          cudaStream_t s);
+
+// Preconditioner (k_precond.cu).  Tables are per instance, FP64 and FP32.
+struct PrecTables {
+  int nx, ny, nt;
+  double *Hx64, *Hy64, *Vt64, *lamt64, *L1_64, *L2_64;  // device, FP64
+  float *Hx32, *Hy32, *Vt32, *lamt32, *L1_32, *L2_32;   // device, FP32
+};
+int build_prec_tables(const mfg_problem& p, const Geom& g, PrecTables* t, std::string* err);
+void free_prec_tables(PrecTables* t);
+// z = P^{-1} r.  work64: 2n doubles (FP64 path); work32: 2n floats (mixed path).
+void launch_precond(const Geom& g, const PrecTables& t, int precision, const double* r, double* z,
+                    double* work64, float* work32, const DevScalars* sc, cudaStream_t s);
+int precond_kernel_count(const Geom& g);
+int precond_configure();
+
+// Prox (k_prox.cu).
+void launch_prox_cp(const Geom& g, const Coef& cf, const double* z, double* y, double* ybar,
+                    const double* V, const double* W, double* partials, DevScalars* sc,
+                    cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
+void launch_prox_plain(const Geom& g, const Coef& cf, double tau, const double* v, double* y,
+                       const double* V, const double* W, cudaStream_t s);
+
+}  // namespace mfg

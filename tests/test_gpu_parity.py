@@ -1,0 +1,199 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
+same seeded inputs: operators, preconditioner, prox and the CP iterate.
+
+Tolerances: operator applies are single FP64 stencil evaluations, compared in
+relative l2 and l_inf at 1e-12.  The preconditioner solve z = P^{-1} r is
+compared by its normwise backward error
+  eta = ||P z - r||_inf / (||P||_inf ||z||_inf + ||r||_inf)
+against the oracle's assembled P: orthonormal transforms make the apply
+backward stable with eta = O(N u), u the unit round-off of the transforms
+(1e-12 for FP64, 5e-5 for FP32), while the forward error also carries the
+condition number of P (up to ~1e8 here), so it is checked only loosely.
+The CP iterate after a fixed count is compared at 1e-8 relative l2 (the target
+stated for the method, with PCG at relative tolerance 1e-10)."""
+import numpy as np
+import pytest
+
+import mfg_inputs as mi
+from oracle import operators as ops
+from oracle import solvers
+from oracle.cp import Solver
+from oracle.prox import prox as oracle_prox
+
+from _gpu_helpers import dev, host, lib, linf_rel, rel
+
+pytestmark = pytest.mark.gpu
+
+# ragged sizes spanning several 8 x 32 stencil tiles and several time chunks
+CASES = [
+    dict(seed=1, dim=2, nx=19, ny=45, nt=11, bc=("periodic", "periodic")),
+    dict(seed=2, dim=2, nx=17, ny=33, nt=9, bc=("neumann", "neumann")),
+    dict(seed=3, dim=2, nx=10, ny=70, nt=7, bc=("periodic", "neumann")),
+    dict(seed=4, dim=2, nx=25, ny=12, nt=13, bc=("neumann", "periodic")),
+    dict(seed=5, dim=1, nx=67, nt=12, bc=("periodic", "periodic")),
+    dict(seed=6, dim=1, nx=40, nt=9, bc=("neumann", "periodic")),
+]
+
+
+def _inst(case, **kw):
+    c = dict(case)
+    c.update(kw)
+    return mi.small(**c)
+
+
+def _backward_error(A, x, b):
+    res = np.abs(A @ x - b).max()
+    nA = np.abs(A).sum(axis=1).max()
+    return res / (nA * np.abs(x).max() + np.abs(b).max())
+
+
+def _plan(prob, precision="fp64"):
+    return lib().mfg_plan(dict(prob), precision=precision)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_apply_C_Ct_AAt(case):
+    import torch
+    inst = _inst(case)
+    p = inst["problem"]
+    L = lib()
+    plan = _plan(p)
+    s, n, c = ops.sizes(p)
+    C = ops.constraint(p)
+    v = mi.random_field(c * n, 11)
+    pv = mi.random_field(n, 12)
+    r = torch.empty(n, dtype=torch.float64, device="cuda")
+    x = torch.empty(c * n, dtype=torch.float64, device="cuda")
+    q = torch.empty(n, dtype=torch.float64, device="cuda")
+    L.mfg_apply_C(plan, 0, dev(v), r)
+    L.mfg_apply_Ct(plan, 0, dev(pv), x)
+    L.mfg_apply_AAt(plan, 0, dev(pv), q)
+    torch.cuda.synchronize()
+    ref_r, ref_x = C @ v, C.T @ pv
+    ref_q = ops.AAt(p, C) @ pv
+    for got, ref in ((host(r), ref_r), (host(x), ref_x), (host(q), ref_q)):
+        assert rel(got, ref) <= 1e-12
+        assert linf_rel(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("l", [1, 2])
+def test_precond_fp64(case, l):
+    import torch
+    inst = _inst(case, l=l)
+    p = inst["problem"]
+    plan = _plan(p)
+    n = ops.sizes(p)[1]
+    r = mi.random_field(n, 21)
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    lib().mfg_apply_precond(plan, 0, dev(r), z)
+    torch.cuda.synchronize()
+    P = ops.precond(p)
+    zg = host(z)
+    assert _backward_error(P, zg, r) <= 1e-12
+    assert rel(zg, solvers.solve_direct(P, r)) <= 1e-6
+
+
+@pytest.mark.parametrize("case", CASES[:4])
+def test_precond_fp32(case):
+    import torch
+    inst = _inst(case, l=1)
+    p = inst["problem"]
+    plan = _plan(p, "mixed")
+    n = ops.sizes(p)[1]
+    r = mi.random_field(n, 22)
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    lib().mfg_apply_precond(plan, 0, dev(r), z)
+    torch.cuda.synchronize()
+    P = ops.precond(p)
+    zg = host(z)
+    assert _backward_error(P, zg, r) <= 5e-5
+    assert rel(zg, solvers.solve_direct(P, r)) <= 1e-2
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_prox(case):
+    import torch
+    inst = _inst(case)
+    p = inst["problem"]
+    plan = _plan(p)
+    s, n, c = ops.sizes(p)
+    v = mi.random_field((c, p["nt"]) + tuple(p["n"]), 31, -2.0, 2.0)
+    v[0] += 0.5
+    y = torch.empty(c * n, dtype=torch.float64, device="cuda")
+    for tau in (0.05, 1.0):
+        lib().mfg_prox(plan, 0, tau, dev(v), dev(inst["V"]), dev(inst["W"]), y)
+        torch.cuda.synchronize()
+        ref = oracle_prox(p, tau, v, inst["V"], inst["W"]).reshape(-1)
+        got = host(y)
+        assert np.abs(got - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+        assert np.all(got[:n] >= 0)
+
+
+def _gpu_cp(inst, iters, precision="fp64", cg_tol=1e-10):
+    import torch
+    p = dict(inst["problem"], max_cp=iters, cg_tol=cg_tol)
+    L = lib()
+    plan = L.mfg_plan(p, precision=precision)
+    y = dev(inst["y0"])
+    ybar = y.clone()
+    z = torch.zeros(ops.sizes(p)[1], dtype=torch.float64, device="cuda")
+    rc, st = L.mfg_solve(plan, dev(inst["m0"]), dev(inst["V"]), dev(inst["W"]), y, ybar, z)
+    return rc, st[0], host(y), host(ybar), host(z)
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cp_iterate(case, precision):
+    """PCG at 1e-12 so that the comparison isolates the implementation.
+
+    Bound: max(1e-8, 10 kappa u) with kappa = cond(AAt) and u = 2^-53.  Every
+    exact solve with AAt carries a relative error up to ~kappa u, and the oracle's
+    own two exact solvers (LU and spatially diagonalised) already differ by that
+    much on the stiffest case here (kappa ~ 1e8)."""
+    inst = _inst(case)
+    p = inst["problem"]
+    iters = 25
+    rc, st, y, ybar, z = _gpu_cp(inst, iters, precision, cg_tol=1e-12)
+    assert rc == 0 and st.status == 0
+    assert st.cp_iters == iters and st.ell == iters
+    ref = Solver(p, inst["m0"], inst["V"], inst["W"], method="modal").run(inst["y0"], iters=iters)
+    ev = np.linalg.eigvalsh(ops.AAt(p).toarray())
+    tol = max(1e-8, 10 * (ev.max() / ev.min()) * 2.0 ** -53)
+    n = ops.sizes(p)[1]
+    assert rel(y, ref["y"]) <= tol
+    assert rel(y[:n], ref["y"][0]) <= tol
+    assert rel(ybar, ref["ybar"]) <= tol
+    C = ops.constraint(p)
+    assert rel(C.T @ z, ref["x"]) <= tol
+    assert abs(st.tau - ref["tau"]) <= 1e-14 * ref["tau"]
+    assert abs(st.sigma - ref["sigma"]) <= 1e-14 * ref["sigma"]
+
+
+def test_cp_resume_matches_single_run():
+    import torch
+    inst = _inst(CASES[0])
+    p = dict(inst["problem"], max_cp=10)
+    L = lib()
+    plan = L.mfg_plan(p)
+    m0, V, W = dev(inst["m0"]), dev(inst["V"]), dev(inst["W"])
+    y = dev(inst["y0"]); ybar = y.clone()
+    z = torch.zeros(ops.sizes(p)[1], dtype=torch.float64, device="cuda")
+    rc, st = L.mfg_solve(plan, m0, V, W, y, ybar, z)
+    rc, st = L.mfg_solve(plan, m0, V, W, y, ybar, z, stats=st)
+    assert st[0].ell == 20
+    _, st2, y2, _, _ = _gpu_cp(inst, 20)
+    assert rel(host(y), y2) <= 1e-13
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config1_fixed_count(precision):
+    """1-D periodic workload, 300 CP iterations, PCG at 1e-10: iterate vs oracle."""
+    inst = mi.config1()
+    p = inst["problem"]
+    rc, st, y, ybar, z = _gpu_cp(inst, 300, precision, cg_tol=1e-10)
+    assert rc == 0 and st.cp_iters == 300
+    ref = Solver(p, inst["m0"], inst["V"], inst["W"]).run(inst["y0"], iters=300)
+    err = rel(y, ref["y"])
+    print(f"config1 {precision}: rel err {err:.3e}, PCG iterations {st.cg_iters}")
+    assert err <= 1e-8
