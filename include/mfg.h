@@ -173,6 +173,7 @@ long long mfg_kernel_launches(mfg_plan_t plan);
 enum { MFG_LAUNCH_GRAPH = 0, MFG_LAUNCH_EAGER = 1 };
 int mfg_set_launch_mode(mfg_plan_t plan, int mode);
 
+
 #ifdef __cplusplus
 }
 #endif

@@ -236,3 +236,4 @@ def mfg_apply_Ct(plan, b, p, x, stream=None):
 
 def mfg_set_launch_mode(plan, mode):
     _check(LIB.mfg_set_launch_mode(plan.handle, {"graph": MFG_LAUNCH_GRAPH, "eager": MFG_LAUNCH_EAGER}.get(mode, mode)))
+

@@ -24,13 +24,17 @@
 using namespace mfg;
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
 
-int fail(int code, const std::string& msg) {
+int mfg::set_error(int code, const std::string& msg) {
   g_last_error = msg;
   return code;
 }
+
+namespace {
+
+int fail(int code, const std::string& msg) { return mfg::set_error(code, msg); }
 
 #define CK(call)                                                                              \
   do {                                                                                        \
@@ -53,55 +57,37 @@ struct Inst {
 
 }  // namespace
 
-struct mfg_plan_s {
-  int device = 0;
-  std::vector<Inst> inst;
-  size_t field_total = 0, primal_total = 0, dual_total = 0;
-  DevScalars* sc_dev = nullptr;
-  DevScalars* sc_host = nullptr;  // pinned
-  long long launches = 0;
-  // graph cache
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  const void* key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  cudaStream_t cap0 = nullptr, cap1 = nullptr;
-  int launch_mode = MFG_LAUNCH_GRAPH;
-  // device staging for mfg_solve_host
-  double *h_m0 = nullptr, *h_V = nullptr, *h_W = nullptr, *h_y = nullptr, *h_ybar = nullptr,
-         *h_z = nullptr;
-};
+namespace mfg {
 
-namespace {
-
-int validate(const mfg_problem& p, int idx) {
+int validate_problem(const mfg_problem& p, int idx) {
   const std::string at = " (instance " + std::to_string(idx) + ")";
-  if (p.dim != 1 && p.dim != 2) return fail(MFG_ERR_INVALID_ARG, "dim must be 1 or 2" + at);
+  if (p.dim != 1 && p.dim != 2) return set_error(MFG_ERR_INVALID_ARG, "dim must be 1 or 2" + at);
   if (p.qprime != 2.0)
-    return fail(MFG_ERR_UNSUPPORTED, "only the quadratic Hamiltonian q' = 2 is built" + at);
+    return set_error(MFG_ERR_UNSUPPORTED, "only the quadratic Hamiltonian q' = 2 is built" + at);
   for (int a = 0; a < p.dim; ++a) {
-    if (p.n[a] < 2) return fail(MFG_ERR_INVALID_ARG, "grid sizes must be >= 2" + at);
-    if (!(p.len[a] > 0.0)) return fail(MFG_ERR_INVALID_ARG, "domain lengths must be > 0" + at);
+    if (p.n[a] < 2) return set_error(MFG_ERR_INVALID_ARG, "grid sizes must be >= 2" + at);
+    if (!(p.len[a] > 0.0)) return set_error(MFG_ERR_INVALID_ARG, "domain lengths must be > 0" + at);
     if (p.bc[a] != MFG_PERIODIC && p.bc[a] != MFG_NEUMANN)
-      return fail(MFG_ERR_INVALID_ARG, "bc must be MFG_PERIODIC or MFG_NEUMANN" + at);
+      return set_error(MFG_ERR_INVALID_ARG, "bc must be MFG_PERIODIC or MFG_NEUMANN" + at);
   }
-  if (p.nt < 2) return fail(MFG_ERR_INVALID_ARG, "nt must be >= 2" + at);
-  if (p.nt > kMaxNt) return fail(MFG_ERR_UNSUPPORTED, "nt above 256 is not built" + at);
-  if (!(p.T > 0.0)) return fail(MFG_ERR_INVALID_ARG, "T must be > 0" + at);
-  if (!(p.nu >= 0.0)) return fail(MFG_ERR_INVALID_ARG, "nu must be >= 0" + at);
+  if (p.nt < 2) return set_error(MFG_ERR_INVALID_ARG, "nt must be >= 2" + at);
+  if (p.nt > kMaxNt) return set_error(MFG_ERR_UNSUPPORTED, "nt above 256 is not built" + at);
+  if (!(p.T > 0.0)) return set_error(MFG_ERR_INVALID_ARG, "T must be > 0" + at);
+  if (!(p.nu >= 0.0)) return set_error(MFG_ERR_INVALID_ARG, "nu must be >= 0" + at);
   if (!(p.f_a >= 0.0) || !(p.f_b >= 0.0) || !(p.g_a >= 0.0))
-    return fail(MFG_ERR_INVALID_ARG, "f_a, f_b, g_a must be >= 0 (monotone couplings)" + at);
-  if (p.l != 1 && p.l != 2) return fail(MFG_ERR_INVALID_ARG, "l must be 1 or 2" + at);
+    return set_error(MFG_ERR_INVALID_ARG, "f_a, f_b, g_a must be >= 0 (monotone couplings)" + at);
+  if (p.l != 1 && p.l != 2) return set_error(MFG_ERR_INVALID_ARG, "l must be 1 or 2" + at);
   if (!(p.gamma > 0.0) || !(p.tau0 > 0.0) || !(p.sigma0 > 0.0))
-    return fail(MFG_ERR_INVALID_ARG, "gamma, tau0, sigma0 must be > 0" + at);
-  if (p.max_cp < 0 || p.max_cg < 1) return fail(MFG_ERR_INVALID_ARG, "max_cp >= 0, max_cg >= 1" + at);
+    return set_error(MFG_ERR_INVALID_ARG, "gamma, tau0, sigma0 must be > 0" + at);
+  if (p.max_cp < 0 || p.max_cg < 1) return set_error(MFG_ERR_INVALID_ARG, "max_cp >= 0, max_cg >= 1" + at);
   if (p.cg_rule != MFG_CG_FIXED && p.cg_rule != MFG_CG_ADAPTIVE)
-    return fail(MFG_ERR_INVALID_ARG, "cg_rule must be MFG_CG_FIXED or MFG_CG_ADAPTIVE" + at);
+    return set_error(MFG_ERR_INVALID_ARG, "cg_rule must be MFG_CG_FIXED or MFG_CG_ADAPTIVE" + at);
   if (p.cg_rule == MFG_CG_FIXED && !(p.cg_tol > 0.0))
-    return fail(MFG_ERR_INVALID_ARG, "cg_tol must be > 0" + at);
+    return set_error(MFG_ERR_INVALID_ARG, "cg_tol must be > 0" + at);
   if (p.precision != MFG_FP64 && p.precision != MFG_MIXED)
-    return fail(MFG_ERR_INVALID_ARG, "precision must be MFG_FP64 or MFG_MIXED" + at);
+    return set_error(MFG_ERR_INVALID_ARG, "precision must be MFG_FP64 or MFG_MIXED" + at);
   const double nxy = (double)p.n[0] * (p.dim == 2 ? p.n[1] : 1);
-  if (nxy * p.nt > 4.0e9) return fail(MFG_ERR_INVALID_ARG, "instance too large" + at);
+  if (nxy * p.nt > 4.0e9) return set_error(MFG_ERR_INVALID_ARG, "instance too large" + at);
   return MFG_OK;
 }
 
@@ -140,6 +126,28 @@ Geom make_geom(const mfg_problem& p) {
   g.n = (long long)g.S * g.nt;
   return g;
 }
+
+}  // namespace mfg
+
+struct mfg_plan_s {
+  int device = 0;
+  std::vector<Inst> inst;
+  size_t field_total = 0, primal_total = 0, dual_total = 0;
+  DevScalars* sc_dev = nullptr;
+  DevScalars* sc_host = nullptr;  // pinned
+  long long launches = 0;
+  // graph cache
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void* key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t cap0 = nullptr, cap1 = nullptr;
+  int launch_mode = MFG_LAUNCH_GRAPH;
+  // device staging for mfg_solve_host
+  double *h_m0 = nullptr, *h_V = nullptr, *h_W = nullptr, *h_y = nullptr, *h_ybar = nullptr,
+         *h_z = nullptr;
+};
+
+namespace {
 
 void free_inst(Inst& in) {
   free_prec_tables(&in.tabs);
@@ -298,7 +306,7 @@ int mfg_plan(const mfg_problem* probs, int batch, mfg_plan_t* out) {
   *out = nullptr;
   if (!probs || batch < 1) return fail(MFG_ERR_INVALID_ARG, "need at least one problem");
   for (int b = 0; b < batch; ++b) {
-    int rc = validate(probs[b], b);
+    int rc = validate_problem(probs[b], b);
     if (rc != MFG_OK) return rc;
   }
   g_last_error.clear();

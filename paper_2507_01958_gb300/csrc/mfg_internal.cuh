@@ -54,6 +54,12 @@ struct DevScalars {
   unsigned int pad;
 };
 
+// Host helpers (mfg_api.cu): problem validation (sets the error text),
+// internal geometry, and the thread-local error record.
+int validate_problem(const mfg_problem& p, int idx);
+Geom make_geom(const mfg_problem& p);
+int set_error(int code, const std::string& msg);
+
 // Grid-stride 1-D launch shape shared by reduction kernels.
 inline int red_blocks(long long n) {
   long long b = (n + kThreads - 1) / kThreads;

@@ -1,0 +1,65 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point that
+include/mfg.h declares, and the ctypes structs match the C layout."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mfg.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|long long|const char\*)\s+(mfg_\w+)\s*\(", txt, re.M)))
+
+
+def _lib():
+    import paper_2507_01958_gb300 as pkg
+    so = os.path.join(ROOT, "paper_2507_01958_gb300", "libmfg_gb300.so")
+    if not os.path.exists(so):
+        pkg.build()
+    return pkg.lib()
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib()
+    decl = _declared()
+    assert len(decl) >= 15
+    for name in decl:
+        assert hasattr(L.LIB, name), name
+        assert name in L.EXPORTED, name
+    out = subprocess.run(["nm", "-D", "--defined-only", L.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (mfg_\w+)", out))
+    assert set(decl) <= exported
+
+
+def test_struct_layout_matches_header(tmp_path):
+    import ctypes
+    L = _lib()
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mfg.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(mfg_problem), '
+                   'sizeof(mfg_stats), offsetof(mfg_problem, precision), offsetof(mfg_problem, nu), '
+                   'offsetof(mfg_stats, cg_iters), offsetof(mfg_stats, sigma));return 0;}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert vals == [ctypes.sizeof(L.MfgProblem), ctypes.sizeof(L.MfgStats),
+                    L.MfgProblem.precision.offset, L.MfgProblem.nu.offset,
+                    L.MfgStats.cg_iters.offset, L.MfgStats.sigma.offset]
+
+
+def test_plan_rejects_invalid_problems_without_gpu():
+    """Validation happens on the host before any device call."""
+    import mfg_inputs as mi
+    L = _lib()
+    base = mi.small(1)["problem"]
+    for bad, code in ((dict(base, qprime=1.5), L.MFG_ERR_UNSUPPORTED), (dict(base, nt=1), L.MFG_ERR_INVALID_ARG),
+                      (dict(base, nu=-1.0), L.MFG_ERR_INVALID_ARG), (dict(base, l=3), L.MFG_ERR_INVALID_ARG),
+                      (dict(base, f_a=-0.1), L.MFG_ERR_INVALID_ARG), (dict(base, nt=300), L.MFG_ERR_UNSUPPORTED)):
+        with pytest.raises(L.MfgError) as e:
+            L.mfg_plan(bad)
+        assert e.value.code == code
+        assert L.mfg_last_error()
