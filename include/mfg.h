@@ -173,6 +173,27 @@ long long mfg_kernel_launches(mfg_plan_t plan);
 enum { MFG_LAUNCH_GRAPH = 0, MFG_LAUNCH_EAGER = 1 };
 int mfg_set_launch_mode(mfg_plan_t plan, int mode);
 
+/* z = P^{-1} r for the single problem *p, like mfg_apply_precond, but with no
+ * plan and no device memory allocation of any kind.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate device
+ * memory where they call it: work being recorded into a CUDA graph under
+ * global stream capture (where cudaMalloc is not permitted), code whose memory
+ * belongs to a pool or framework allocator it may not bypass, and latency-
+ * critical paths that cannot risk an allocation's cost or failure.  Those
+ * callers cannot use mfg_plan, which allocates.
+ *   - Scratch: the transform tables and work buffers live in one static
+ *     device array of 6.4 MB that every GPU loading this library holds until
+ *     the process exits.  Limits: N_t*Nx*Ny <= 262144, Nx, Ny <= 256,
+ *     N_t <= 128; larger problems return MFG_ERR_INVALID_ARG with a message.
+ *   - The first call on each device resolves the array's device address and
+ *     sets kernel attributes; make that first call before any stream capture.
+ *   - All calls share the array and each call rewrites all of it that it
+ *     reads, so no state carries over; but calls whose work overlaps on the
+ *     GPU (other streams or other threads) race and corrupt each other.
+ *     Calls on one stream are ordered and safe.
+ *   - r, z: n device doubles, caller-owned, must not alias.  Precision as in
+ *     p->precision.  Stream-ordered; returns after enqueueing. */
+int mfg_apply_precond_noalloc(const mfg_problem* p, const double* r, double* z, void* stream);
 
 #ifdef __cplusplus
 }

@@ -65,6 +65,7 @@ def _load():
         "mfg_apply_Ct": ([P, I, V, V, V], I),
         "mfg_kernel_launches": ([P], C.c_longlong),
         "mfg_set_launch_mode": ([P, I], I),
+        "mfg_apply_precond_noalloc": ([C.POINTER(MfgProblem), V, V, V], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -76,7 +77,8 @@ def _load():
 LIB = _load()
 EXPORTED = ("mfg_plan", "mfg_destroy", "mfg_last_error", "mfg_layout", "mfg_sizes", "mfg_solve",
             "mfg_solve_host", "mfg_apply_precond", "mfg_prox", "mfg_apply_AAt", "mfg_apply_C",
-            "mfg_apply_Ct", "mfg_kernel_launches", "mfg_set_launch_mode")
+            "mfg_apply_Ct", "mfg_kernel_launches", "mfg_set_launch_mode",
+            "mfg_apply_precond_noalloc")
 
 
 def mfg_last_error():
@@ -237,3 +239,10 @@ def mfg_apply_Ct(plan, b, p, x, stream=None):
 def mfg_set_launch_mode(plan, mode):
     _check(LIB.mfg_set_launch_mode(plan.handle, {"graph": MFG_LAUNCH_GRAPH, "eager": MFG_LAUNCH_EAGER}.get(mode, mode)))
 
+
+def mfg_apply_precond_noalloc(problem, r, z, stream=None, precision=None):
+    """z = P^{-1} r for one problem dict without a plan and without allocating
+    device memory (static library scratch; see include/mfg.h)."""
+    p = problem_struct(problem, precision)
+    n = p.nt * p.n[0] * (p.n[1] if p.dim == 2 else 1)
+    _check(LIB.mfg_apply_precond_noalloc(C.byref(p), _ptr(r, n), _ptr(z, n), _stream(stream)))
