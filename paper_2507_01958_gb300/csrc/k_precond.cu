@@ -16,9 +16,10 @@
 //
 // Passes over the data (ping-pong work buffers, 10n words in total):
 //   y-forward, x-forward, [time forward, divide by S, time inverse] fused,
-//   x-inverse, y-inverse.  Each spatial pass is a small dense matrix applied
-//   along one axis (a SIMT GEMM with the transform matrix on the left); the
-//   time pass keeps a 32-column strip of all N_t planes in shared memory.
+//   x-inverse, y-inverse.  A spatial pass is an FFT (k_fft.cu) when the axis
+//   length is a power of two from 8 to 512, otherwise a small dense matrix
+//   applied along the axis (a SIMT GEMM with the transform matrix on the
+//   left); the time pass keeps a strip of all N_t planes in shared memory.
 #include <cmath>
 #include <vector>
 
@@ -111,6 +112,13 @@ int build_prec_tables(const mfg_problem& p, const Geom& g, PrecTables* t, std::s
     *err = "transform tables failed the orthonormality check";
     return MFG_ERR_INVALID_ARG;
   }
+  double asym = 0.0;
+  for (int a = 0; a < g.nt; ++a)
+    for (int b = 0; b < g.nt; ++b) asym = std::fmax(asym, std::fabs(V[(size_t)a * g.nt + b] - V[(size_t)b * g.nt + a]));
+  if (asym > 1e-12) {
+    *err = "time transform table is not symmetric";
+    return MFG_ERR_INVALID_ARG;
+  }
   std::vector<double> L1((size_t)g.S), L2((size_t)g.S);
   const double dtv = 1.0 / g.idt, nu = g.nu;
   for (int a = 0; a < g.nx; ++a)
@@ -131,7 +139,28 @@ int build_prec_tables(const mfg_problem& p, const Geom& g, PrecTables* t, std::s
   t->lamt32 = upload<float>(lt, err);
   t->L1_32 = upload<float>(L1, err);
   t->L2_32 = upload<float>(L2, err);
-  if (!t->Hx64 || !t->Hy64 || !t->Vt64 || !t->lamt64 || !t->L1_64 || !t->L2_64 || !t->Hx32 ||
+  // FFT twiddles: tw[m] = (cos, sin)(2 pi m/N), dct[k] = (cos, sin)(pi k/(2N)).
+  auto fft_tables = [&](int N, double** tw64, float** tw32, double** dc64, float** dc32) {
+    if (!fft_supported(N)) return true;
+    const double pi = 3.14159265358979323846;
+    std::vector<double> tw((size_t)N), dc((size_t)2 * N);
+    for (int m = 0; m < N / 2; ++m) {
+      tw[2 * m] = std::cos(2.0 * pi * m / N);
+      tw[2 * m + 1] = std::sin(2.0 * pi * m / N);
+    }
+    for (int k = 0; k < N; ++k) {
+      dc[2 * k] = std::cos(pi * k / (2.0 * N));
+      dc[2 * k + 1] = std::sin(pi * k / (2.0 * N));
+    }
+    *tw64 = upload<double>(tw, err);
+    *tw32 = upload<float>(tw, err);
+    *dc64 = upload<double>(dc, err);
+    *dc32 = upload<float>(dc, err);
+    return *tw64 && *tw32 && *dc64 && *dc32;
+  };
+  const bool fft_ok = (g.nx == 1 || fft_tables(g.nx, &t->twx64, &t->twx32, &t->dctx64, &t->dctx32)) &&
+                      fft_tables(g.ny, &t->twy64, &t->twy32, &t->dcty64, &t->dcty32);
+  if (!fft_ok || !t->Hx64 || !t->Hy64 || !t->Vt64 || !t->lamt64 || !t->L1_64 || !t->L2_64 || !t->Hx32 ||
       !t->Hy32 || !t->Vt32 || !t->lamt32 || !t->L1_32 || !t->L2_32) {
     free_prec_tables(t);
     return MFG_ERR_CUDA;
@@ -140,8 +169,9 @@ int build_prec_tables(const mfg_problem& p, const Geom& g, PrecTables* t, std::s
 }
 
 void free_prec_tables(PrecTables* t) {
-  void* ptrs[] = {t->Hx64, t->Hy64, t->Vt64, t->lamt64, t->L1_64, t->L2_64,
-                  t->Hx32, t->Hy32, t->Vt32, t->lamt32, t->L1_32, t->L2_32};
+  void* ptrs[] = {t->Hx64, t->Hy64, t->Vt64, t->lamt64, t->L1_64, t->L2_64, t->Hx32, t->Hy32,
+                  t->Vt32, t->lamt32, t->L1_32, t->L2_32, t->twx64, t->twx32, t->dctx64, t->dctx32,
+                  t->twy64, t->twy32, t->dcty64, t->dcty32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   *t = PrecTables{};
@@ -322,46 +352,163 @@ __global__ void __launch_bounds__(256) k_time(const T* __restrict__ in, T* __res
   }
 }
 
+// Fixed-N_t time pass: the whole (symmetric, orthonormal) time matrix V sits in
+// shared memory next to an N_t x TW strip; each thread owns an RM x RN register
+// tile, so one pass over b costs RM + RN shared loads for RM * RN FMAs.  Both
+// DCT-VIII and DST-I are symmetric (V = V^T, checked on the host), so rows of V
+// serve the forward and the inverse product.
+template <typename T, int NT>
+struct TimeShape {
+  static constexpr int TW = (NT >= 128) ? 32 : 64;       // strip width (spatial modes)
+  static constexpr int RN = 4;                            // columns per thread
+  static constexpr int CG = TW / RN;                      // column groups
+  static constexpr int RG = 256 / CG;                     // row groups
+  static constexpr int RM = NT / RG;                      // rows per thread
+  static constexpr size_t smem = sizeof(T) * ((size_t)NT * NT + (size_t)NT * TW);
+};
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(256) k_time_fast(const T* __restrict__ in, T* __restrict__ out,
+                                                   const T* __restrict__ V, const T* __restrict__ lamt,
+                                                   const T* __restrict__ L1, const T* __restrict__ L2,
+                                                   int S, const DevScalars* sc) {
+  if (sc != nullptr && sc->cg_done) return;
+  using Sh = TimeShape<T, NT>;
+  constexpr int TW = Sh::TW, RN = Sh::RN, CG = Sh::CG, RM = Sh::RM;
+  extern __shared__ unsigned char smem_raw[];
+  T* Vs = reinterpret_cast<T*>(smem_raw);  // [NT][NT]
+  T* X = Vs + NT * NT;                      // [NT][TW]
+  const int tid = threadIdx.x;
+  const int cg = tid % CG, rg = tid / CG;
+  const int s0 = blockIdx.x * TW;
+  for (int q = tid; q < NT * NT; q += 256) Vs[q] = V[q];
+  for (int q = tid; q < NT * TW; q += 256) {
+    const int k = q / TW, c = q % TW;
+    X[q] = (s0 + c < S) ? in[(long long)k * S + s0 + c] : T(0);
+  }
+  __syncthreads();
+  T acc[RM][RN];
+#pragma unroll
+  for (int u = 0; u < RM; ++u)
+#pragma unroll
+    for (int v = 0; v < RN; ++v) acc[u][v] = T(0);
+  // Y = V X: row r = rg + RG*u uses V[r][b] = V[b][r]
+#pragma unroll 4
+  for (int b = 0; b < NT; ++b) {
+    T xv[RN], vv[RM];
+#pragma unroll
+    for (int v = 0; v < RN; ++v) xv[v] = X[b * TW + cg * RN + v];
+#pragma unroll
+    for (int u = 0; u < RM; ++u) vv[u] = Vs[b * NT + rg + Sh::RG * u];
+#pragma unroll
+    for (int u = 0; u < RM; ++u)
+#pragma unroll
+      for (int v = 0; v < RN; ++v) acc[u][v] = fma(vv[u], xv[v], acc[u][v]);
+  }
+  __syncthreads();
+  // divide by S(k, s) = Lambda_1(s) + lambda_k Lambda_2(s); Y overwrites X
+#pragma unroll
+  for (int v = 0; v < RN; ++v) {
+    const int c = cg * RN + v;
+    const int s = s0 + c;
+    const T l1 = s < S ? L1[s] : T(1), l2 = s < S ? L2[s] : T(0);
+#pragma unroll
+    for (int u = 0; u < RM; ++u) {
+      const int r = rg + Sh::RG * u;
+      X[r * TW + c] = acc[u][v] / (l1 + lamt[r] * l2);
+      acc[u][v] = T(0);
+    }
+  }
+  __syncthreads();
+  // out = V^T Y: out[a][c] = sum_b V[b][a] Y[b][c]
+#pragma unroll 4
+  for (int b = 0; b < NT; ++b) {
+    T yv[RN], vv[RM];
+#pragma unroll
+    for (int v = 0; v < RN; ++v) yv[v] = X[b * TW + cg * RN + v];
+#pragma unroll
+    for (int u = 0; u < RM; ++u) vv[u] = Vs[b * NT + rg + Sh::RG * u];
+#pragma unroll
+    for (int u = 0; u < RM; ++u)
+#pragma unroll
+      for (int v = 0; v < RN; ++v) acc[u][v] = fma(vv[u], yv[v], acc[u][v]);
+  }
+#pragma unroll
+  for (int u = 0; u < RM; ++u) {
+    const int r = rg + Sh::RG * u;
+#pragma unroll
+    for (int v = 0; v < RN; ++v) {
+      const int s = s0 + cg * RN + v;
+      if (s < S) out[(long long)r * S + s] = acc[u][v];
+    }
+  }
+}
+
+template <typename T, int NT>
+static void launch_time_fast(const T* in, T* out, const T* V, const T* lamt, const T* L1, const T* L2,
+                             int S, const DevScalars* sc, cudaStream_t s) {
+  using Sh = TimeShape<T, NT>;
+  k_time_fast<T, NT><<<(S + Sh::TW - 1) / Sh::TW, 256, Sh::smem, s>>>(in, out, V, lamt, L1, L2, S, sc);
+}
+
 template <typename T>
 static size_t time_smem(int nt) { return sizeof(T) * (size_t)nt * (TSW + TCH); }
 
 template <typename T>
 static void time_pass(const T* in, T* out, const T* V, const T* lamt, const T* L1, const T* L2,
                       int nt, int S, const DevScalars* sc, cudaStream_t s) {
+  if (nt == 32) return launch_time_fast<T, 32>(in, out, V, lamt, L1, L2, S, sc, s);
+  if (nt == 64) return launch_time_fast<T, 64>(in, out, V, lamt, L1, L2, S, sc, s);
+  if (nt == 128) return launch_time_fast<T, 128>(in, out, V, lamt, L1, L2, S, sc, s);
   const size_t sm = time_smem<T>(nt);
   k_time<T><<<(S + TSW - 1) / TSW, 256, sm, s>>>(in, out, V, lamt, L1, L2, nt, S, sc);
 }
 
 template <typename T>
 static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, const T* lamt,
-                          const T* L1, const T* L2, const double* r, double* z, T* w0, T* w1,
+                          const T* L1, const T* L2, const T* twx, const T* dctx, const T* twy,
+                          const T* dcty, const double* r, double* z, T* w0, T* w1,
                           const DevScalars* sc, cudaStream_t s) {
   const long long S = g.S, n = g.n;
+  const bool fy = twy != nullptr && fft_supported(g.ny);
+  const bool fx = twx != nullptr && fft_supported(g.nx);
   // y forward: axis length ny, contiguous
-  axis_pass<double, T, T>(r, w0, Hy, g.ny, 1, n / g.ny, 0, sc, s);
+  if (fy)
+    fft_y_forward<T>(g.ny, g.pery, r, w0, twy, dcty, n / g.ny, sc, s);
+  else
+    axis_pass<double, T, T>(r, w0, Hy, g.ny, 1, n / g.ny, 0, sc, s);
   T* a = w0;
   T* b = w1;
   if (g.nx > 1) {
-    axis_pass<T, T, T>(a, b, Hx, g.nx, g.ny, (long long)g.nt, 0, sc, s);
+    if (fx)
+      fft_x<T>(g.nx, g.perx, 0, a, b, twx, dctx, g.ny, (long long)g.nt, sc, s);
+    else
+      axis_pass<T, T, T>(a, b, Hx, g.nx, g.ny, (long long)g.nt, 0, sc, s);
     T* t = a; a = b; b = t;
   }
   time_pass<T>(a, b, V, lamt, L1, L2, g.nt, (int)S, sc, s);
   { T* t = a; a = b; b = t; }
   if (g.nx > 1) {
-    axis_pass<T, T, T>(a, b, Hx, g.nx, g.ny, (long long)g.nt, 1, sc, s);
+    if (fx)
+      fft_x<T>(g.nx, g.perx, 1, a, b, twx, dctx, g.ny, (long long)g.nt, sc, s);
+    else
+      axis_pass<T, T, T>(a, b, Hx, g.nx, g.ny, (long long)g.nt, 1, sc, s);
     T* t = a; a = b; b = t;
   }
-  axis_pass<T, T, double>(a, z, Hy, g.ny, 1, n / g.ny, 1, sc, s);
+  if (fy)
+    fft_y_inverse<T>(g.ny, g.pery, a, z, twy, dcty, n / g.ny, sc, s);
+  else
+    axis_pass<T, T, double>(a, z, Hy, g.ny, 1, n / g.ny, 1, sc, s);
 }
 
 void launch_precond(const Geom& g, const PrecTables& t, int precision, const double* r, double* z,
                     double* work64, float* work32, const DevScalars* sc, cudaStream_t s) {
   if (precision == MFG_MIXED)
-    precond_typed<float>(g, t.Hx32, t.Hy32, t.Vt32, t.lamt32, t.L1_32, t.L2_32, r, z, work32,
-                         work32 + g.n, sc, s);
+    precond_typed<float>(g, t.Hx32, t.Hy32, t.Vt32, t.lamt32, t.L1_32, t.L2_32, t.twx32, t.dctx32,
+                         t.twy32, t.dcty32, r, z, work32, work32 + g.n, sc, s);
   else
-    precond_typed<double>(g, t.Hx64, t.Hy64, t.Vt64, t.lamt64, t.L1_64, t.L2_64, r, z, work64,
-                          work64 + g.n, sc, s);
+    precond_typed<double>(g, t.Hx64, t.Hy64, t.Vt64, t.lamt64, t.L1_64, t.L2_64, t.twx64, t.dctx64,
+                          t.twy64, t.dcty64, r, z, work64, work64 + g.n, sc, s);
 }
 
 int precond_kernel_count(const Geom& g) { return g.nx > 1 ? 5 : 3; }
@@ -373,7 +520,15 @@ int precond_configure() {
                                         (int)time_smem<double>(kMaxNt));
   cudaError_t e2 = cudaFuncSetAttribute(k_time<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)time_smem<float>(kMaxNt));
-  return (e1 == cudaSuccess && e2 == cudaSuccess) ? MFG_OK : MFG_ERR_CUDA;
+  int bad = (e1 != cudaSuccess) || (e2 != cudaSuccess);
+#define MFG_TF_ATTR(T, NT)                                                                    \
+  bad |= cudaFuncSetAttribute(k_time_fast<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                              (int)TimeShape<T, NT>::smem) != cudaSuccess;
+  MFG_TF_ATTR(float, 32) MFG_TF_ATTR(float, 64) MFG_TF_ATTR(float, 128)
+  MFG_TF_ATTR(double, 32) MFG_TF_ATTR(double, 64) MFG_TF_ATTR(double, 128)
+#undef MFG_TF_ATTR
+  bad |= fft_configure() != MFG_OK;
+  return bad ? MFG_ERR_CUDA : MFG_OK;
 }
 
 }  // namespace mfg

@@ -92,6 +92,10 @@ struct PrecTables {
   int nx, ny, nt;
   double *Hx64, *Hy64, *Vt64, *lamt64, *L1_64, *L2_64;  // device, FP64
   float *Hx32, *Hy32, *Vt32, *lamt32, *L1_32, *L2_32;   // device, FP32
+  // FFT twiddles for power-of-two axes (null otherwise): tw (N/2 complex),
+  // dct (N complex) per axis, both precisions.
+  double *twx64 = nullptr, *dctx64 = nullptr, *twy64 = nullptr, *dcty64 = nullptr;
+  float *twx32 = nullptr, *dctx32 = nullptr, *twy32 = nullptr, *dcty32 = nullptr;
 };
 int build_prec_tables(const mfg_problem& p, const Geom& g, PrecTables* t, std::string* err);
 void free_prec_tables(PrecTables* t);
@@ -100,6 +104,19 @@ void launch_precond(const Geom& g, const PrecTables& t, int precision, const dou
                     double* work64, float* work32, const DevScalars* sc, cudaStream_t s);
 int precond_kernel_count(const Geom& g);
 int precond_configure();
+
+// FFT spatial passes (k_fft.cu).
+bool fft_supported(int N);
+int fft_configure();
+template <typename T>
+void fft_y_forward(int N, int periodic, const double* in, T* out, const T* tw, const T* dct,
+                   long long nlines, const DevScalars* sc, cudaStream_t s);
+template <typename T>
+void fft_y_inverse(int N, int periodic, const T* in, double* out, const T* tw, const T* dct,
+                   long long nlines, const DevScalars* sc, cudaStream_t s);
+template <typename T>
+void fft_x(int N, int periodic, int inverse, const T* in, T* out, const T* tw, const T* dct,
+           long long inner, long long outer, const DevScalars* sc, cudaStream_t s);
 
 // Prox (k_prox.cu).
 void launch_prox_cp(const Geom& g, const Coef& cf, const double* z, double* y, double* ybar,

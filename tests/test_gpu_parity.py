@@ -35,6 +35,17 @@ CASES = [
 ]
 
 
+# power-of-two axes take the FFT spatial passes; N_t in {32, 64} the fixed-size time pass
+POW2 = [
+    dict(seed=21, dim=2, nx=16, ny=32, nt=32, bc=("periodic", "periodic")),
+    dict(seed=22, dim=2, nx=32, ny=8, nt=64, bc=("neumann", "neumann")),
+    dict(seed=23, dim=2, nx=8, ny=64, nt=16, bc=("periodic", "neumann")),
+    dict(seed=24, dim=2, nx=64, ny=16, nt=8, bc=("neumann", "periodic")),
+    dict(seed=25, dim=1, nx=128, nt=32, bc=("neumann", "periodic")),
+    dict(seed=26, dim=1, nx=256, nt=32, bc=("periodic", "periodic")),
+]
+
+
 def _inst(case, **kw):
     c = dict(case)
     c.update(kw)
@@ -76,7 +87,7 @@ def test_apply_C_Ct_AAt(case):
         assert linf_rel(got, ref) <= 1e-12
 
 
-@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("case", CASES + POW2)
 @pytest.mark.parametrize("l", [1, 2])
 def test_precond_fp64(case, l):
     import torch
@@ -94,7 +105,7 @@ def test_precond_fp64(case, l):
     assert rel(zg, solvers.solve_direct(P, r)) <= 1e-6
 
 
-@pytest.mark.parametrize("case", CASES[:4])
+@pytest.mark.parametrize("case", CASES[:4] + POW2)
 def test_precond_fp32(case):
     import torch
     inst = _inst(case, l=1)
@@ -142,7 +153,7 @@ def _gpu_cp(inst, iters, precision="fp64", cg_tol=1e-10):
     return rc, st[0], host(y), host(ybar), host(z)
 
 
-@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("case", CASES + POW2[:3])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_cp_iterate(case, precision):
     """PCG at 1e-12 so that the comparison isolates the implementation.
