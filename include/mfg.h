@@ -160,6 +160,24 @@ int mfg_apply_C(mfg_plan_t plan, int b, const double* v, double* r, void* stream
 /* x = C^T p for instance b; p: n, x: c*n. */
 int mfg_apply_Ct(mfg_plan_t plan, int b, const double* p, double* x, void* stream);
 
+/* Gradient of a loss on the converged equilibrium of instance b by implicit
+ * differentiation of the optimality (KKT) conditions of (VMFG_h) (Sec. 2-3:
+ * the fixed point y = prox_{tau phi}(y - tau C^T z), C y = d(m0)).
+ *   y, z   : a converged solution from mfg_solve (c*n and n device doubles);
+ *            the active set is read off y (m > 0, w components != 0)
+ *   gy     : dloss/dy, c*n device doubles (same layout as y)
+ *   dm0    : out, dloss/dm0, Nx*Ny           dV : out, dloss/dV(x), Nx*Ny
+ *   dW     : out, dloss/dW(x), Nx*Ny or NULL dnu: out, dloss/dnu, 1 device double
+ *   tol, max_iter: relative tolerance and cap of the adjoint PCG
+ *   st     : out; cg_iters = adjoint PCG iterations, r_last = final relative residual
+ * The adjoint system is solved through its Schur complement
+ * C_A H^{-1} C_A^T with the plan's preconditioner P (eq. prec) inside PCG,
+ * H being the per-cell Hessian of phi.  The first call allocates a c*n + n
+ * workspace owned by the plan.  Synchronises `stream`. */
+int mfg_adjoint(mfg_plan_t plan, int b, const double* y, const double* z, const double* gy,
+                double* dm0, double* dV, double* dW, double* dnu, double tol, int max_iter,
+                mfg_stats* st, void* stream);
+
 /* Number of kernel launches the library enqueued since the plan was made
  * (graph nodes executed by mfg_solve are counted per execution). */
 long long mfg_kernel_launches(mfg_plan_t plan);

@@ -65,6 +65,7 @@ def _load():
         "mfg_apply_Ct": ([P, I, V, V, V], I),
         "mfg_kernel_launches": ([P], C.c_longlong),
         "mfg_set_launch_mode": ([P, I], I),
+        "mfg_adjoint": ([P, I, V, V, V, V, V, V, V, D, I, C.POINTER(MfgStats), V], I),
         "mfg_apply_precond_noalloc": ([C.POINTER(MfgProblem), V, V, V], I),
     }
     for name, (args, res) in sig.items():
@@ -77,7 +78,7 @@ def _load():
 LIB = _load()
 EXPORTED = ("mfg_plan", "mfg_destroy", "mfg_last_error", "mfg_layout", "mfg_sizes", "mfg_solve",
             "mfg_solve_host", "mfg_apply_precond", "mfg_prox", "mfg_apply_AAt", "mfg_apply_C",
-            "mfg_apply_Ct", "mfg_kernel_launches", "mfg_set_launch_mode",
+            "mfg_apply_Ct", "mfg_kernel_launches", "mfg_set_launch_mode", "mfg_adjoint",
             "mfg_apply_precond_noalloc")
 
 
@@ -110,9 +111,10 @@ def problem_struct(d, precision=None):
 class Plan:
     """Owns an mfg_plan_t; freed with mfg_destroy."""
 
-    def __init__(self, handle, batch):
+    def __init__(self, handle, batch, nts=()):
         self.handle = C.c_void_p(handle)
         self.batch = batch
+        self.nts = list(nts)
 
     def close(self):
         if self.handle:
@@ -132,7 +134,7 @@ def mfg_plan(problems, precision=None):
     arr = (MfgProblem * len(problems))(*[problem_struct(d, precision) for d in problems])
     h = C.c_void_p()
     _check(LIB.mfg_plan(arr, len(problems), C.byref(h)))
-    return Plan(h.value, len(problems))
+    return Plan(h.value, len(problems), [d["nt"] for d in problems])
 
 
 def mfg_destroy(plan):
@@ -207,6 +209,24 @@ def mfg_solve_host(plan, m0, V, W, y, ybar, z, stats=None, stream=None):
     if rc not in (MFG_OK, MFG_ERR_NOT_CONVERGED, MFG_ERR_NONFINITE):
         _check(rc)
     return rc, stats
+
+
+def mfg_adjoint(plan, b, y, z, gy, dm0, dV, dW, dnu, tol=1e-10, max_iter=5000, stream=None):
+    """Implicit-differentiation gradient at a converged solution (see mfg.h)."""
+    lay = mfg_layout(plan, b)
+    n, cn = lay["n"], lay["n"] * lay["c"]
+    S = n // plan_nt(plan, b)
+    st = MfgStats()
+    rc = LIB.mfg_adjoint(plan.handle, b, _ptr(y, cn), _ptr(z, n), _ptr(gy, cn), _ptr(dm0, S), _ptr(dV, S),
+                         _ptr(dW, S) if dW is not None else C.c_void_p(), _ptr(dnu, 1), float(tol),
+                         int(max_iter), C.byref(st), _stream(stream))
+    if rc not in (MFG_OK, MFG_ERR_NOT_CONVERGED):
+        _check(rc)
+    return rc, st
+
+
+def plan_nt(plan, b):
+    return plan.nts[b]
 
 
 def mfg_apply_precond(plan, b, r, z, stream=None):

@@ -46,11 +46,17 @@ __device__ __forceinline__ int wrap_or_neg(int i, int N, int per) {
 // mode 0: r = alpha * (C v - d), d = m0/dt on plane 0 when m0 != nullptr.
 // mode 1: CP right-hand side r = sigma (C v - d) with sigma from the device
 //         scalars; reduces ||r||^2, resets the PCG state for the new solve.
+// mode 2: PCG step of the adjoint Schur system: r = C v, reduces pdot.r,
+//         alpha = rz/(pdot.r).
+// mode 3: adjoint right-hand side r = C v; reduces ||r||^2, resets the PCG
+//         state with the fixed tolerance.
 template <int ACTX>
 __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __restrict__ v,
                                                       double* __restrict__ r, double alpha,
                                                       const double* __restrict__ m0,
+                                                      const double* __restrict__ pdot,
                                                       double* partials, DevScalars* sc, int mode) {
+  if (mode == 2 && sc->cg_done) return;
   if (mode == 1) alpha = sc->sigma;
   const long long n = g.n;
   const double* m = v;
@@ -84,14 +90,28 @@ __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __re
     if (m0 != nullptr && k == 0) val -= m0[(long long)i * g.ny + j] * g.idt;
     val *= alpha;
     r[e] = val;
-    acc += val * val;
+    acc += (mode == 2) ? pdot[e] * val : val * val;
   }
-  if (mode != 1) return;
+  if (mode == 0) return;
   double part[1] = {acc};
   block_sum<1>(part);
   if (!publish_and_check_last<1>(part, partials, &sc->counter)) return;
   double tot[1];
   gather_partials<1>(partials, tot);
+  if (mode == 2) {
+    if (flat_tid() == 0) {
+      sc->pq = tot[0];
+      if (tot[0] > 0.0 && isfinite(tot[0])) {
+        sc->alpha = sc->rz / tot[0];
+      } else {
+        sc->alpha = 0.0;
+        sc->cg_done = 1;
+        if (sc->status == MFG_OK) sc->status = MFG_ERR_NONFINITE;
+      }
+      sc->counter = 0;
+    }
+    return;
+  }
   if (flat_tid() == 0) {
     sc->bnorm2 = tot[0];
     sc->cg_it = 0;
@@ -109,12 +129,12 @@ __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __re
 }
 
 void launch_apply_C(const Geom& g, const double* v, double* r, double alpha, const double* m0,
-                    double* partials, DevScalars* sc, int mode, cudaStream_t s) {
+                    double* partials, DevScalars* sc, int mode, cudaStream_t s, const double* pdot) {
   const int nb = red_blocks(g.n);
   if (g.actx)
-    k_apply_C<1><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, partials, sc, mode);
+    k_apply_C<1><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, pdot, partials, sc, mode);
   else
-    k_apply_C<0><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, partials, sc, mode);
+    k_apply_C<0><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, pdot, partials, sc, mode);
 }
 
 // ----------------------------------------------------------------- C^T p --

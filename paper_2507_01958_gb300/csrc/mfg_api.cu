@@ -53,6 +53,7 @@ struct Inst {
   float* work32 = nullptr;
   double* partials = nullptr;
   DevScalars* sc = nullptr;  // points into the plan's contiguous array
+  double *adj_t = nullptr, *adj_eta = nullptr;  // adjoint workspace, allocated on first use
 };
 
 }  // namespace
@@ -151,10 +152,10 @@ namespace {
 
 void free_inst(Inst& in) {
   free_prec_tables(&in.tabs);
-  void* ptrs[] = {in.r, in.pv, in.q, in.zp, in.work64, in.work32, in.partials};
+  void* ptrs[] = {in.r, in.pv, in.q, in.zp, in.work64, in.work32, in.partials, in.adj_t, in.adj_eta};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  in.r = in.pv = in.q = in.zp = in.work64 = in.partials = nullptr;
+  in.r = in.pv = in.q = in.zp = in.work64 = in.partials = in.adj_t = in.adj_eta = nullptr;
   in.work32 = nullptr;
 }
 
@@ -492,6 +493,66 @@ int mfg_solve_host(mfg_plan_t pl, const double* m0, const double* V, const doubl
   CK(cudaMemcpyAsync(z, pl->h_z, D, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return rc;
+}
+
+int mfg_adjoint(mfg_plan_t pl, int b, const double* y, const double* z, const double* gy, double* dm0,
+                double* dV, double* dW, double* dnu, double tol, int max_iter, mfg_stats* st,
+                void* stream) {
+  int rc = check_b(pl, b);
+  if (rc != MFG_OK) return rc;
+  if (!y || !z || !gy || !dm0 || !dV || !dnu || !st)
+    return fail(MFG_ERR_INVALID_ARG, "null array or stats pointer");
+  if (!(tol > 0.0) || max_iter < 1) return fail(MFG_ERR_INVALID_ARG, "tol > 0 and max_iter >= 1 required");
+  Inst& in = pl->inst[b];
+  const Geom& g = in.g;
+  const size_t n = (size_t)g.n;
+  if (!in.adj_t) {
+    if (cudaMalloc(&in.adj_t, (size_t)g.c * n * 8) != cudaSuccess || cudaMalloc(&in.adj_eta, n * 8) != cudaSuccess)
+      return fail(MFG_ERR_CUDA, "cudaMalloc failed for adjoint workspace");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  DevScalars h{};
+  h.status = MFG_OK;
+  h.cg_rule = MFG_CG_FIXED;
+  h.cg_tol_fixed = tol;
+  h.max_cg = max_iter;
+  CK(cudaMemcpyAsync(in.sc, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  const int flex = in.p.precision == MFG_MIXED;
+  // right-hand side C H^{-1} g; eta starts at 0
+  launch_hinv(g, in.cf, y, gy, in.adj_t, s);
+  launch_apply_C(g, in.adj_t, in.r, 1.0, nullptr, in.partials, in.sc, 3, s);
+  CK(cudaMemsetAsync(in.adj_eta, 0, n * 8, s));
+  launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s);
+  launch_init_p(g.n, in.zp, in.pv, in.r, in.partials, in.sc, s);
+  long long launches = 3 + precond_kernel_count(g);
+  DevScalars hs;
+  for (;;) {
+    CK(cudaMemcpyAsync(&hs, in.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs.cg_done) break;
+    launch_ct_hinv(g, in.cf, y, in.pv, nullptr, in.adj_t, s, in.sc);
+    launch_apply_C(g, in.adj_t, in.q, 1.0, nullptr, in.partials, in.sc, 2, s, in.pv);
+    launch_update_zr(g.n, in.adj_eta, in.r, in.pv, in.q, in.partials, in.sc, s);
+    launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s);
+    launch_dot_beta(g.n, in.r, in.zp, in.q, flex, in.partials, in.sc, s);
+    launch_update_p(g.n, in.zp, in.pv, in.sc, 0, 0, s);
+    launches += 5 + precond_kernel_count(g);
+  }
+  // mu = H^{-1}(g - C^T eta), then the contractions
+  launch_ct_hinv(g, in.cf, y, in.adj_eta, gy, in.adj_t, s, nullptr);
+  launch_adj_grads(g, y, z, in.adj_eta, in.adj_t, dm0, dV, dW, dnu, in.partials, in.sc, s);
+  launches += 2;
+  pl->launches += launches;
+  CK(cudaMemcpyAsync(&hs, in.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  std::memset(st, 0, sizeof(*st));
+  st->status = hs.status;
+  st->cg_iters = hs.cg_it;
+  st->max_cg_in_solve = hs.cg_it;
+  st->r_last = hs.bnorm2 > 0 ? std::sqrt(hs.rr / hs.bnorm2) : 0.0;
+  if (hs.status != MFG_OK) return fail(hs.status, "adjoint PCG finished with a non-OK status");
+  return MFG_OK;
 }
 
 int mfg_apply_precond(mfg_plan_t pl, int b, const double* r, double* z, void* stream) {

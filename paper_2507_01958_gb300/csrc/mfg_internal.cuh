@@ -69,7 +69,8 @@ inline int red_blocks(long long n) {
 // ---------------------------------------------------------------- kernels --
 // Stencils (k_stencil.cu).
 void launch_apply_C(const Geom& g, const double* v, double* r, double alpha, const double* m0,
-                    double* partials, DevScalars* sc, int mode, cudaStream_t s);
+                    double* partials, DevScalars* sc, int mode, cudaStream_t s,
+                    const double* pdot = nullptr);
 void launch_apply_Ct(const Geom& g, const double* p, double* x, cudaStream_t s);
 void launch_AAt(const Geom& g, const double* p, double* q, double* partials, DevScalars* sc,
                 int mode, cudaStream_t s);
@@ -117,6 +118,15 @@ void fft_y_inverse(int N, int periodic, const T* in, double* out, const T* tw, c
 template <typename T>
 void fft_x(int N, int periodic, int inverse, const T* in, T* out, const T* tw, const T* dct,
            long long inner, long long outer, const DevScalars* sc, cudaStream_t s);
+
+// Adjoint (k_adjoint.cu).
+void launch_hinv(const Geom& g, const Coef& cf, const double* y, const double* u, double* out,
+                 cudaStream_t s);
+void launch_ct_hinv(const Geom& g, const Coef& cf, const double* y, const double* p,
+                    const double* gsub, double* out, cudaStream_t s, const DevScalars* sc);
+void launch_adj_grads(const Geom& g, const double* y, const double* z, const double* eta,
+                      const double* mu, double* dm0, double* dV, double* dW, double* dnu,
+                      double* partials, DevScalars* sc, cudaStream_t s);
 
 // Prox (k_prox.cu).
 void launch_prox_cp(const Geom& g, const Coef& cf, const double* z, double* y, double* ybar,
