@@ -11,6 +11,8 @@
 //   q = AAt p; alpha = rz/(p.q); z += alpha p; r -= alpha q;
 //   stop if ||r|| <= tol ||r_0||;  zp = P^{-1} r;
 //   beta = (r.zp)/rz (FR)  or  -alpha (q.zp)/rz (PR);  rz = r.zp;  p = zp + beta p.
+#include <cstdint>
+
 #include "mfg_internal.cuh"
 #include "reduce.cuh"
 
@@ -19,17 +21,51 @@ namespace mfg {
 #define GRID_STRIDE(e, n) \
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (n); e += (long long)gridDim.x * blockDim.x)
 
+// The vector kernels walk the data in pairs of doubles and use 16-byte accesses
+// when every operand is 16-byte aligned (twice the bytes in flight per
+// thread), single doubles otherwise.  Both paths visit the elements in the same
+// order, so results do not depend on alignment (a batched instance at an odd
+// offset gives the same bits as the same instance alone).
+__device__ __forceinline__ bool aligned16(const void* a, const void* b = nullptr, const void* c = nullptr,
+                                          const void* d = nullptr) {
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(c) |
+           reinterpret_cast<uintptr_t>(d)) & 15) == 0;
+}
+
+#define PAIR_LOOP(n, BODY2, BODY1, vec)                                                          \
+  {                                                                                              \
+    const long long n2_ = (n) >> 1;                                                              \
+    _Pragma("unroll 4")                                                                          \
+    for (long long e2 = blockIdx.x * (long long)blockDim.x + threadIdx.x; e2 < n2_;              \
+         e2 += (long long)gridDim.x * blockDim.x) {                                              \
+      if (vec) {                                                                                 \
+        BODY2                                                                                    \
+      } else {                                                                                   \
+        { const long long e = 2 * e2; BODY1 }                                                    \
+        { const long long e = 2 * e2 + 1; BODY1 }                                                \
+      }                                                                                          \
+    }                                                                                            \
+    if (((n) & 1) && blockIdx.x == 0 && threadIdx.x == 0) { const long long e = (n) - 1; BODY1 } \
+  }
+
 // p = zp, rz = r.zp (start of a solve, after the first preconditioner apply).
 __global__ void __launch_bounds__(kThreads) k_init_p(long long n, const double* __restrict__ zp,
                                                      double* __restrict__ p, const double* __restrict__ r,
                                                      double* partials, DevScalars* sc) {
   if (sc->cg_done) return;
   double acc = 0.0;
-  GRID_STRIDE(e, n) {
+  const bool vec = aligned16(zp, p, r);
+  PAIR_LOOP(n, {
+    const double2 v = reinterpret_cast<const double2*>(zp)[e2];
+    reinterpret_cast<double2*>(p)[e2] = v;
+    const double2 rv = reinterpret_cast<const double2*>(r)[e2];
+    acc = fma(rv.x, v.x, acc);
+    acc = fma(rv.y, v.y, acc);
+  }, {
     const double v = zp[e];
     p[e] = v;
-    acc += r[e] * v;
-  }
+    acc = fma(r[e], v, acc);
+  }, vec)
   double part[1] = {acc};
   block_sum<1>(part);
   if (!publish_and_check_last<1>(part, partials, &sc->counter)) return;
@@ -54,12 +90,26 @@ __global__ void __launch_bounds__(kThreads) k_update_zr(long long n, double* __r
   if (sc->cg_done) return;
   const double alpha = sc->alpha;
   double acc = 0.0;
-  GRID_STRIDE(e, n) {
-    z[e] += alpha * p[e];
-    const double rv = r[e] - alpha * q[e];
+  const bool vec = aligned16(z, r, p, q);
+  PAIR_LOOP(n, {
+    double2 zv = reinterpret_cast<double2*>(z)[e2];
+    const double2 pv = reinterpret_cast<const double2*>(p)[e2];
+    double2 rv = reinterpret_cast<double2*>(r)[e2];
+    const double2 qv = reinterpret_cast<const double2*>(q)[e2];
+    zv.x = fma(alpha, pv.x, zv.x);
+    zv.y = fma(alpha, pv.y, zv.y);
+    rv.x = fma(-alpha, qv.x, rv.x);
+    rv.y = fma(-alpha, qv.y, rv.y);
+    reinterpret_cast<double2*>(z)[e2] = zv;
+    reinterpret_cast<double2*>(r)[e2] = rv;
+    acc = fma(rv.x, rv.x, acc);
+    acc = fma(rv.y, rv.y, acc);
+  }, {
+    z[e] = fma(alpha, p[e], z[e]);
+    const double rv = fma(-alpha, q[e], r[e]);
     r[e] = rv;
-    acc += rv * rv;
-  }
+    acc = fma(rv, rv, acc);
+  }, vec)
   double part[1] = {acc};
   block_sum<1>(part);
   if (!publish_and_check_last<1>(part, partials, &sc->counter)) return;
@@ -90,11 +140,22 @@ __global__ void __launch_bounds__(kThreads) k_dot_beta(long long n, const double
                                                        DevScalars* sc) {
   if (sc->cg_done) return;
   double a0 = 0.0, a1 = 0.0;
-  GRID_STRIDE(e, n) {
+  const bool vec = aligned16(r, zp, q);
+  PAIR_LOOP(n, {
+    const double2 zv = reinterpret_cast<const double2*>(zp)[e2];
+    const double2 rv = reinterpret_cast<const double2*>(r)[e2];
+    a0 = fma(rv.x, zv.x, a0);
+    a0 = fma(rv.y, zv.y, a0);
+    if (FLEX) {
+      const double2 qv = reinterpret_cast<const double2*>(q)[e2];
+      a1 = fma(qv.x, zv.x, a1);
+      a1 = fma(qv.y, zv.y, a1);
+    }
+  }, {
     const double zv = zp[e];
-    a0 += r[e] * zv;
-    if (FLEX) a1 += q[e] * zv;
-  }
+    a0 = fma(r[e], zv, a0);
+    if (FLEX) a1 = fma(q[e], zv, a1);
+  }, vec)
   double part[2] = {a0, a1};
   block_sum<2>(part);
   if (!publish_and_check_last<2>(part, partials, &sc->counter)) return;
@@ -121,7 +182,14 @@ __global__ void __launch_bounds__(kThreads) k_update_p(long long n, const double
   if (use_handle && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, done ? 0u : 1u);
   if (done) return;
   const double beta = sc->beta;
-  GRID_STRIDE(e, n) { p[e] = zp[e] + beta * p[e]; }
+  const bool vec = aligned16(zp, p);
+  PAIR_LOOP(n, {
+    const double2 zv = reinterpret_cast<const double2*>(zp)[e2];
+    double2 pv = reinterpret_cast<double2*>(p)[e2];
+    pv.x = fma(beta, pv.x, zv.x);
+    pv.y = fma(beta, pv.y, zv.y);
+    reinterpret_cast<double2*>(p)[e2] = pv;
+  }, { p[e] = fma(beta, p[e], zp[e]); }, vec)
 }
 
 void launch_init_p(long long n, const double* zp, double* p, const double* r, double* partials,

@@ -17,6 +17,7 @@
 // The result equals the dense orthonormal transform of the plan's tables to
 // round-off; the pass reads and writes each element once.
 #include "mfg_internal.cuh"
+#include "reduce.cuh"
 
 namespace mfg {
 
@@ -29,24 +30,42 @@ enum { FFT_DHT = 0, FFT_DCT2 = 1, FFT_DCT3 = 2 };
 
 template <typename T, int N>
 struct FftShape {
-  static constexpr int CL = (sizeof(T) == 8 && N > 256) ? 8 : 16;  // complex lines per block
+  static constexpr int CL = 8;       // complex lines per block (one per warp)
   static constexpr int LB = 2 * CL;                                 // real lines per block
-  static constexpr size_t smem = 2 * (size_t)CL * N * sizeof(cx<T>);
+  static constexpr int NP = N + 1;  // padded line stride: staging across lines hits distinct banks
+  static constexpr size_t smem = 2 * (size_t)CL * NP * sizeof(cx<T>) + (size_t)(N / 2 + N) * sizeof(cx<T>);
+};
+
+// Dot products fused into the last pass of a PCG preconditioner apply: while
+// zp = P^{-1} r is stored, r.zp (and q.zp for the flexible variant) are
+// accumulated and the last block forms beta exactly as k_dot_beta does.
+struct DotFuse {
+  const double* r;
+  const double* q;
+  double* partials;
+  DevScalars* sc;
+  int flex;
 };
 
 // tw[m] = (cos 2 pi m/N, sin 2 pi m/N), m < N/2;  dct[k] = (cos pi k/(2N), sin pi k/(2N)).
-template <typename T, int N, int MODE, bool CONTIG, typename TI, typename TO>
+template <typename T, int N, int MODE, bool CONTIG, typename TI, typename TO, bool DOT = false>
 __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __restrict__ out,
                                              const T* __restrict__ tw, const T* __restrict__ dct,
-                                             long long inner, long long nlines, const DevScalars* sc) {
+                                             long long inner, long long nlines, const DevScalars* sc,
+                                             DotFuse df) {
   if (sc != nullptr && sc->cg_done) return;
   using Sh = FftShape<T, N>;
-  constexpr int CL = Sh::CL, LB = Sh::LB;
+  constexpr int CL = Sh::CL, LB = Sh::LB, NP = Sh::NP;
   extern __shared__ unsigned char smem_raw[];
   cx<T>* buf0 = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* buf1 = buf0 + CL * N;
-  T* real1 = reinterpret_cast<T*>(buf1);  // [LB][N] real staging in buf1
+  cx<T>* buf1 = buf0 + CL * NP;
+  T* real1 = reinterpret_cast<T*>(buf1);  // [LB][NP] real staging in buf1
+  cx<T>* tws = buf1 + CL * NP;            // twiddles, N/2
+  cx<T>* dcs = tws + N / 2;               // DCT phases, N
   const int tid = threadIdx.x;
+  for (int q = tid; q < N / 2; q += 256) tws[q] = cx<T>{tw[2 * q], tw[2 * q + 1]};
+  if (MODE != FFT_DHT)
+    for (int q = tid; q < N; q += 256) dcs[q] = cx<T>{dct[2 * q], dct[2 * q + 1]};
   const long long line0 = (long long)blockIdx.x * LB;
   const long long o = blockIdx.y;
 
@@ -61,10 +80,10 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
       v = (T)in[addr];
     }
     if (MODE == FFT_DCT3) {
-      real1[l * N + i] = v;
+      real1[l * NP + i] = v;
     } else {
       const int p = (MODE == FFT_DCT2) ? ((i & 1) ? N - 1 - (i >> 1) : (i >> 1)) : i;
-      T* dst = reinterpret_cast<T*>(&buf0[(l >> 1) * N + p]);
+      T* dst = reinterpret_cast<T*>(&buf0[(l >> 1) * NP + p]);
       dst[l & 1] = v;
     }
   }
@@ -74,15 +93,15 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
     const T s0 = T(1) / sqrt(T(N)), s1 = T(1) / sqrt(T(2 * N));
     for (int idx = tid; idx < CL * N; idx += 256) {
       const int q = idx / N, k = idx % N;
-      const T* xa = real1 + (2 * q) * N;
-      const T* xb = real1 + (2 * q + 1) * N;
+      const T* xa = real1 + (2 * q) * NP;
+      const T* xb = real1 + (2 * q + 1) * NP;
       const T sk = k == 0 ? s0 : s1, sm = s1;  // N-k > 0 whenever k > 0
       const T ak = xa[k] * sk, bk = xb[k] * sk;
       const T am = k == 0 ? T(0) : xa[N - k] * sm, bm = k == 0 ? T(0) : xb[N - k] * sm;
-      const T c = dct[2 * k], s = dct[2 * k + 1];
+      const T c = dcs[k].x, s = dcs[k].y;
       const T war = c * ak + s * am, wai = s * ak - c * am;
       const T wbr = c * bk + s * bm, wbi = s * bk - c * bm;
-      buf0[q * N + k] = cx<T>{war - wbi, wai + wbr};
+      buf0[q * NP + k] = cx<T>{war - wbi, wai + wbr};
     }
     __syncthreads();
   }
@@ -93,13 +112,14 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
   int log2n = 0;
   for (int t = N; t > 1; t >>= 1) ++log2n;
   for (int q = warp; q < CL; q += 8) {
-    cx<T>* src = buf0 + q * N;
-    cx<T>* dst = buf1 + q * N;
+    cx<T>* src = buf0 + q * NP;
+    cx<T>* dst = buf1 + q * NP;
     for (int Ns = 1; Ns < N; Ns <<= 1) {
       for (int j = lane; j < N / 2; j += 32) {
         const int k = j & (Ns - 1);
         const int m = k * (N / (2 * Ns));
-        const T wc = tw[2 * m], ws = sgn * tw[2 * m + 1];
+        const cx<T> tk = tws[m];
+        const T wc = tk.x, ws = sgn * tk.y;
         const cx<T> a = src[j];
         const cx<T> b0 = src[j + N / 2];
         const cx<T> b{b0.x * wc - b0.y * ws, b0.x * ws + b0.y * wc};
@@ -113,61 +133,95 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
   }
   __syncthreads();
   const cx<T>* Z = (log2n & 1) ? buf1 : buf0;
-  T* R = reinterpret_cast<T*>((log2n & 1) ? buf0 : buf1);  // real output staging [LB][N]
+  T* R = reinterpret_cast<T*>((log2n & 1) ? buf0 : buf1);  // real output staging [LB][NP]
 
   // ---- separate the packed pairs and finish the transform
   const T rsn = T(1) / sqrt(T(N));
   for (int idx = tid; idx < CL * N; idx += 256) {
     const int q = idx / N, k = idx % N;
-    const cx<T> zk = Z[q * N + k];
+    const cx<T> zk = Z[q * NP + k];
     if (MODE == FFT_DCT3) {
       const int pos = (k < N / 2) ? 2 * k : 2 * (N - 1 - k) + 1;
-      R[(2 * q) * N + pos] = zk.x;
-      R[(2 * q + 1) * N + pos] = zk.y;
+      R[(2 * q) * NP + pos] = zk.x;
+      R[(2 * q + 1) * NP + pos] = zk.y;
     } else {
-      const cx<T> zm = Z[q * N + ((N - k) & (N - 1))];
+      const cx<T> zm = Z[q * NP + ((N - k) & (N - 1))];
       const T sr = T(0.5) * (zk.x + zm.x), si = T(0.5) * (zk.y - zm.y);  // X_a
       const T dr = T(0.5) * (zk.y + zm.y), di = T(0.5) * (zm.x - zk.x);  // X_b
       if (MODE == FFT_DHT) {
-        R[(2 * q) * N + k] = (sr - si) * rsn;
-        R[(2 * q + 1) * N + k] = (dr - di) * rsn;
+        R[(2 * q) * NP + k] = (sr - si) * rsn;
+        R[(2 * q + 1) * NP + k] = (dr - di) * rsn;
       } else {
         const T ck = k == 0 ? T(1) / sqrt(T(N)) : sqrt(T(2) / T(N));
-        const T c = dct[2 * k], s = dct[2 * k + 1];
-        R[(2 * q) * N + k] = ck * (c * sr + s * si);
-        R[(2 * q + 1) * N + k] = ck * (c * dr + s * di);
+        const T c = dcs[k].x, s = dcs[k].y;
+        R[(2 * q) * NP + k] = ck * (c * sr + s * si);
+        R[(2 * q + 1) * NP + k] = ck * (c * dr + s * di);
       }
     }
   }
   __syncthreads();
 
-  // ---- store
+  // ---- store (with the fused dot products of the PCG step when DOT)
+  double a0 = 0.0, a1 = 0.0;
   for (int idx = tid; idx < LB * N; idx += 256) {
     int l, i;
     if (CONTIG) { l = idx / N; i = idx % N; } else { i = idx / LB; l = idx % LB; }
     const long long line = line0 + l;
     if (line < nlines) {
       const long long addr = CONTIG ? line * N + i : (o * N + i) * inner + line;
-      out[addr] = (TO)R[l * N + i];
+      const TO v = (TO)R[l * NP + i];
+      out[addr] = v;
+      if constexpr (DOT) {
+        a0 = fma(df.r[addr], (double)v, a0);
+        if (df.flex) a1 = fma(df.q[addr], (double)v, a1);
+      }
+    }
+  }
+  if constexpr (DOT) {
+    double part[2] = {a0, a1};
+    block_sum<2>(part);
+    if (!publish_and_check_last<2>(part, df.partials, &df.sc->counter)) return;
+    double tot[2];
+    gather_partials<2>(df.partials, tot);
+    if (flat_tid() == 0) {
+      DevScalars* s = df.sc;
+      const double rz_old = s->rz;
+      s->qz = tot[1];
+      s->beta = df.flex ? (-s->alpha * tot[1] / rz_old) : (tot[0] / rz_old);
+      s->rz = tot[0];
+      if (!isfinite(s->beta) || !(tot[0] > 0.0)) {
+        s->cg_done = 1;
+        if (s->status == MFG_OK) s->status = MFG_ERR_NONFINITE;
+      }
+      s->counter = 0;
     }
   }
 }
 
 bool fft_supported(int N) { return N >= 8 && N <= 512 && (N & (N - 1)) == 0; }
 
-template <typename T, int N, int MODE, bool CONTIG, typename TI, typename TO>
-static void launch_one(const TI* in, TO* out, const T* tw, const T* dct, long long inner,
-                       long long outer, long long nlines, const DevScalars* sc, cudaStream_t s) {
-  using Sh = FftShape<T, N>;
-  dim3 grid((unsigned)((nlines + Sh::LB - 1) / Sh::LB), CONTIG ? 1u : (unsigned)outer);
-  k_fft<T, N, MODE, CONTIG, TI, TO><<<grid, 256, Sh::smem, s>>>(in, out, tw, dct, inner, nlines, sc);
+// Partial-sum slots the fused-dot y pass needs (2 per block).
+long long fft_dot_partials(const Geom& g) {
+  const long long lb = FftShape<float, 8>::LB;  // lines per block (same for every N and type)
+  static_assert(FftShape<float, 8>::LB == FftShape<double, 512>::LB, "uniform lines per block");
+  const long long nlines = g.n / g.ny;
+  return 2 * ((nlines + lb - 1) / lb);
 }
 
-template <typename T, int MODE, bool CONTIG, typename TI, typename TO>
+template <typename T, int N, int MODE, bool CONTIG, typename TI, typename TO, bool DOT = false>
+static void launch_one(const TI* in, TO* out, const T* tw, const T* dct, long long inner,
+                       long long outer, long long nlines, const DevScalars* sc, cudaStream_t s,
+                       DotFuse df = DotFuse{}) {
+  using Sh = FftShape<T, N>;
+  dim3 grid((unsigned)((nlines + Sh::LB - 1) / Sh::LB), CONTIG ? 1u : (unsigned)outer);
+  k_fft<T, N, MODE, CONTIG, TI, TO, DOT><<<grid, 256, Sh::smem, s>>>(in, out, tw, dct, inner, nlines, sc, df);
+}
+
+template <typename T, int MODE, bool CONTIG, typename TI, typename TO, bool DOT = false>
 static int set_attr_one() {
   int bad = 0;
 #define MFG_FFT_ATTR(NN)                                                                      \
-  bad |= cudaFuncSetAttribute(k_fft<T, NN, MODE, CONTIG, TI, TO>,                            \
+  bad |= cudaFuncSetAttribute(k_fft<T, NN, MODE, CONTIG, TI, TO, DOT>,                       \
                               cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
                               (int)FftShape<T, NN>::smem) != cudaSuccess;
   MFG_FFT_ATTR(8) MFG_FFT_ATTR(16) MFG_FFT_ATTR(32) MFG_FFT_ATTR(64) MFG_FFT_ATTR(128)
@@ -176,17 +230,16 @@ static int set_attr_one() {
   return bad;
 }
 
-template <typename T, int MODE, bool CONTIG, typename TI, typename TO>
+template <typename T, int MODE, bool CONTIG, typename TI, typename TO, bool DOT = false>
 static void dispatch(int N, const TI* in, TO* out, const T* tw, const T* dct, long long inner,
-                     long long outer, long long nlines, const DevScalars* sc, cudaStream_t s) {
+                     long long outer, long long nlines, const DevScalars* sc, cudaStream_t s,
+                     DotFuse df = DotFuse{}) {
   switch (N) {
-    case 8: launch_one<T, 8, MODE, CONTIG, TI, TO>(in, out, tw, dct, inner, outer, nlines, sc, s); break;
-    case 16: launch_one<T, 16, MODE, CONTIG, TI, TO>(in, out, tw, dct, inner, outer, nlines, sc, s); break;
-    case 32: launch_one<T, 32, MODE, CONTIG, TI, TO>(in, out, tw, dct, inner, outer, nlines, sc, s); break;
-    case 64: launch_one<T, 64, MODE, CONTIG, TI, TO>(in, out, tw, dct, inner, outer, nlines, sc, s); break;
-    case 128: launch_one<T, 128, MODE, CONTIG, TI, TO>(in, out, tw, dct, inner, outer, nlines, sc, s); break;
-    case 256: launch_one<T, 256, MODE, CONTIG, TI, TO>(in, out, tw, dct, inner, outer, nlines, sc, s); break;
-    default: launch_one<T, 512, MODE, CONTIG, TI, TO>(in, out, tw, dct, inner, outer, nlines, sc, s); break;
+#define MFG_FFT_CASE(NN) \
+    case NN: launch_one<T, NN, MODE, CONTIG, TI, TO, DOT>(in, out, tw, dct, inner, outer, nlines, sc, s, df); break;
+    MFG_FFT_CASE(8) MFG_FFT_CASE(16) MFG_FFT_CASE(32) MFG_FFT_CASE(64) MFG_FFT_CASE(128) MFG_FFT_CASE(256)
+#undef MFG_FFT_CASE
+    default: launch_one<T, 512, MODE, CONTIG, TI, TO, DOT>(in, out, tw, dct, inner, outer, nlines, sc, s, df); break;
   }
 }
 
@@ -199,10 +252,19 @@ void fft_y_forward(int N, int periodic, const double* in, T* out, const T* tw, c
   else
     dispatch<T, FFT_DCT2, true, double, T>(N, in, out, tw, dct, 1, 1, nlines, sc, s);
 }
-// y axis, last pass: T in, FP64 out.
+// y axis, last pass: T in, FP64 out; with dot != nullptr the PCG dot products
+// (r.zp, q.zp, beta) are fused into the store.
 template <typename T>
 void fft_y_inverse(int N, int periodic, const T* in, double* out, const T* tw, const T* dct,
-                   long long nlines, const DevScalars* sc, cudaStream_t s) {
+                   long long nlines, const DevScalars* sc, cudaStream_t s, const PcgDot* dot) {
+  if (dot) {
+    DotFuse df{dot->r, dot->q, dot->partials, dot->sc, dot->flex};
+    if (periodic)
+      dispatch<T, FFT_DHT, true, T, double, true>(N, in, out, tw, dct, 1, 1, nlines, sc, s, df);
+    else
+      dispatch<T, FFT_DCT3, true, T, double, true>(N, in, out, tw, dct, 1, 1, nlines, sc, s, df);
+    return;
+  }
   if (periodic)
     dispatch<T, FFT_DHT, true, T, double>(N, in, out, tw, dct, 1, 1, nlines, sc, s);
   else
@@ -225,9 +287,9 @@ template void fft_y_forward<float>(int, int, const double*, float*, const float*
 template void fft_y_forward<double>(int, int, const double*, double*, const double*, const double*, long long,
                                     const DevScalars*, cudaStream_t);
 template void fft_y_inverse<float>(int, int, const float*, double*, const float*, const float*, long long,
-                                   const DevScalars*, cudaStream_t);
+                                   const DevScalars*, cudaStream_t, const PcgDot*);
 template void fft_y_inverse<double>(int, int, const double*, double*, const double*, const double*, long long,
-                                    const DevScalars*, cudaStream_t);
+                                    const DevScalars*, cudaStream_t, const PcgDot*);
 template void fft_x<float>(int, int, int, const float*, float*, const float*, const float*, long long, long long,
                            const DevScalars*, cudaStream_t);
 template void fft_x<double>(int, int, int, const double*, double*, const double*, const double*, long long,
@@ -239,6 +301,10 @@ int fft_configure() {
   bad |= set_attr_one<float, FFT_DCT2, true, double, float>();
   bad |= set_attr_one<float, FFT_DHT, true, float, double>();
   bad |= set_attr_one<float, FFT_DCT3, true, float, double>();
+  bad |= set_attr_one<float, FFT_DHT, true, float, double, true>();
+  bad |= set_attr_one<float, FFT_DCT3, true, float, double, true>();
+  bad |= set_attr_one<double, FFT_DHT, true, double, double, true>();
+  bad |= set_attr_one<double, FFT_DCT3, true, double, double, true>();
   bad |= set_attr_one<float, FFT_DHT, false, float, float>();
   bad |= set_attr_one<float, FFT_DCT2, false, float, float>();
   bad |= set_attr_one<float, FFT_DCT3, false, float, float>();

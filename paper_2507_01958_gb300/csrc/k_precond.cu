@@ -359,13 +359,41 @@ __global__ void __launch_bounds__(256) k_time(const T* __restrict__ in, T* __res
 // serve the forward and the inverse product.
 template <typename T, int NT>
 struct TimeShape {
-  static constexpr int TW = (NT >= 128) ? 32 : 64;       // strip width (spatial modes)
-  static constexpr int RN = 4;                            // columns per thread
+  static constexpr int TW = 32;                           // strip width (spatial modes)
+  static constexpr int RN = 2;                            // columns per thread
   static constexpr int CG = TW / RN;                      // column groups
   static constexpr int RG = 256 / CG;                     // row groups
   static constexpr int RM = NT / RG;                      // rows per thread
   static constexpr size_t smem = sizeof(T) * ((size_t)NT * NT + (size_t)NT * TW);
 };
+
+// K consecutive shared-memory values with the widest aligned vector loads.
+template <int K>
+__device__ __forceinline__ void lds_vec(const float* p, float (&o)[K]) {
+  if constexpr (K % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < K; q += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(p + q);
+      o[q] = v.x; o[q + 1] = v.y; o[q + 2] = v.z; o[q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < K; ++q) o[q] = p[q];
+  }
+}
+template <int K>
+__device__ __forceinline__ void lds_vec(const double* p, double (&o)[K]) {
+  if constexpr (K % 2 == 0) {
+#pragma unroll
+    for (int q = 0; q < K; q += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(p + q);
+      o[q] = v.x; o[q + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < K; ++q) o[q] = p[q];
+  }
+}
 
 template <typename T, int NT>
 __global__ void __launch_bounds__(256) k_time_fast(const T* __restrict__ in, T* __restrict__ out,
@@ -375,11 +403,12 @@ __global__ void __launch_bounds__(256) k_time_fast(const T* __restrict__ in, T* 
   if (sc != nullptr && sc->cg_done) return;
   using Sh = TimeShape<T, NT>;
   constexpr int TW = Sh::TW, RN = Sh::RN, CG = Sh::CG, RM = Sh::RM;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Vs = reinterpret_cast<T*>(smem_raw);  // [NT][NT]
   T* X = Vs + NT * NT;                      // [NT][TW]
   const int tid = threadIdx.x;
   const int cg = tid % CG, rg = tid / CG;
+  const int r0 = rg * RM;  // this thread's rows r0 .. r0 + RM - 1
   const int s0 = blockIdx.x * TW;
   for (int q = tid; q < NT * NT; q += 256) Vs[q] = V[q];
   for (int q = tid; q < NT * TW; q += 256) {
@@ -392,14 +421,12 @@ __global__ void __launch_bounds__(256) k_time_fast(const T* __restrict__ in, T* 
   for (int u = 0; u < RM; ++u)
 #pragma unroll
     for (int v = 0; v < RN; ++v) acc[u][v] = T(0);
-  // Y = V X: row r = rg + RG*u uses V[r][b] = V[b][r]
+  // Y = V X: row r uses V[r][b] = V[b][r] (symmetric V), contiguous in r
 #pragma unroll 4
   for (int b = 0; b < NT; ++b) {
     T xv[RN], vv[RM];
-#pragma unroll
-    for (int v = 0; v < RN; ++v) xv[v] = X[b * TW + cg * RN + v];
-#pragma unroll
-    for (int u = 0; u < RM; ++u) vv[u] = Vs[b * NT + rg + Sh::RG * u];
+    lds_vec<RN>(X + b * TW + cg * RN, xv);
+    lds_vec<RM>(Vs + b * NT + r0, vv);
 #pragma unroll
     for (int u = 0; u < RM; ++u)
 #pragma unroll
@@ -414,7 +441,7 @@ __global__ void __launch_bounds__(256) k_time_fast(const T* __restrict__ in, T* 
     const T l1 = s < S ? L1[s] : T(1), l2 = s < S ? L2[s] : T(0);
 #pragma unroll
     for (int u = 0; u < RM; ++u) {
-      const int r = rg + Sh::RG * u;
+      const int r = r0 + u;
       X[r * TW + c] = acc[u][v] / (l1 + lamt[r] * l2);
       acc[u][v] = T(0);
     }
@@ -424,10 +451,8 @@ __global__ void __launch_bounds__(256) k_time_fast(const T* __restrict__ in, T* 
 #pragma unroll 4
   for (int b = 0; b < NT; ++b) {
     T yv[RN], vv[RM];
-#pragma unroll
-    for (int v = 0; v < RN; ++v) yv[v] = X[b * TW + cg * RN + v];
-#pragma unroll
-    for (int u = 0; u < RM; ++u) vv[u] = Vs[b * NT + rg + Sh::RG * u];
+    lds_vec<RN>(X + b * TW + cg * RN, yv);
+    lds_vec<RM>(Vs + b * NT + r0, vv);
 #pragma unroll
     for (int u = 0; u < RM; ++u)
 #pragma unroll
@@ -435,7 +460,7 @@ __global__ void __launch_bounds__(256) k_time_fast(const T* __restrict__ in, T* 
   }
 #pragma unroll
   for (int u = 0; u < RM; ++u) {
-    const int r = rg + Sh::RG * u;
+    const int r = r0 + u;
 #pragma unroll
     for (int v = 0; v < RN; ++v) {
       const int s = s0 + cg * RN + v;
@@ -468,7 +493,7 @@ template <typename T>
 static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, const T* lamt,
                           const T* L1, const T* L2, const T* twx, const T* dctx, const T* twy,
                           const T* dcty, const double* r, double* z, T* w0, T* w1,
-                          const DevScalars* sc, cudaStream_t s) {
+                          const DevScalars* sc, cudaStream_t s, const PcgDot* dot) {
   const long long S = g.S, n = g.n;
   const bool fy = twy != nullptr && fft_supported(g.ny);
   const bool fx = twx != nullptr && fft_supported(g.nx);
@@ -495,23 +520,32 @@ static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, c
       axis_pass<T, T, T>(a, b, Hx, g.nx, g.ny, (long long)g.nt, 1, sc, s);
     T* t = a; a = b; b = t;
   }
-  if (fy)
-    fft_y_inverse<T>(g.ny, g.pery, a, z, twy, dcty, n / g.ny, sc, s);
-  else
+  if (fy) {
+    fft_y_inverse<T>(g.ny, g.pery, a, z, twy, dcty, n / g.ny, sc, s, dot);
+  } else {
     axis_pass<T, T, double>(a, z, Hy, g.ny, 1, n / g.ny, 1, sc, s);
+    if (dot) launch_dot_beta(n, dot->r, z, dot->q, dot->flex, dot->partials, dot->sc, s);
+  }
 }
 
 void launch_precond(const Geom& g, const PrecTables& t, int precision, const double* r, double* z,
-                    double* work64, float* work32, const DevScalars* sc, cudaStream_t s) {
+                    double* work64, float* work32, const DevScalars* sc, cudaStream_t s,
+                    const PcgDot* dot) {
   if (precision == MFG_MIXED)
     precond_typed<float>(g, t.Hx32, t.Hy32, t.Vt32, t.lamt32, t.L1_32, t.L2_32, t.twx32, t.dctx32,
-                         t.twy32, t.dcty32, r, z, work32, work32 + g.n, sc, s);
+                         t.twy32, t.dcty32, r, z, work32, work32 + g.n, sc, s, dot);
   else
     precond_typed<double>(g, t.Hx64, t.Hy64, t.Vt64, t.lamt64, t.L1_64, t.L2_64, t.twx64, t.dctx64,
-                          t.twy64, t.dcty64, r, z, work64, work64 + g.n, sc, s);
+                          t.twy64, t.dcty64, r, z, work64, work64 + g.n, sc, s, dot);
 }
 
 int precond_kernel_count(const Geom& g) { return g.nx > 1 ? 5 : 3; }
+
+// Kernels of a preconditioner apply that also forms the PCG dot products.
+int precond_dot_kernel_count(const Geom& g, const PrecTables& t) {
+  const bool fused = t.twy32 != nullptr && fft_supported(g.ny);
+  return precond_kernel_count(g) + (fused ? 0 : 1);
+}
 
 // Opt-in shared memory for the time pass; called once per device before any
 // launch or stream capture.

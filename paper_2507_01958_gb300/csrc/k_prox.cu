@@ -61,11 +61,13 @@ template <int NW>
 __device__ __forceinline__ void prox_cell(double mbar, const double (&wbar)[NW], double tau,
                                           double inv_tau, double a, double b, double c, double& m,
                                           double (&w)[NW]) {
+  // projection onto K by sign tests on the bit patterns (no FP64 min/max)
   double P[NW];
   double P2 = 0.0;
 #pragma unroll
   for (int q = 0; q < NW; ++q) {
-    P[q] = (q & 1) ? fmin(wbar[q], 0.0) : fmax(wbar[q], 0.0);
+    const bool neg = __double_as_longlong(wbar[q]) < 0;
+    P[q] = ((q & 1) ? neg : !neg) ? wbar[q] : 0.0;
     P2 = fma(P[q], P[q], P2);
   }
   const double B = mbar - tau * c;
@@ -76,13 +78,21 @@ __device__ __forceinline__ void prox_cell(double mbar, const double (&wbar)[NW],
     for (int q = 0; q < NW; ++q) w[q] = 0.0;
     return;
   }
-  double hi = fmax(0.0, B) + half_P2_tau;
+  double hi = (B > 0.0 ? B : 0.0) + half_P2_tau;
   double lo = 0.0;
   const double hP = 0.5 * tau * P2;
-  const double a1 = 1.0 + tau * a, tb = tau * b;
+  const double a1 = fma(tau, a, 1.0), tb = tau * b;
   const bool fp32_ok = hi < 1e30 && hP < 1e30 && fabs(B) < 1e30 && tau > 1e-30 && tau < 1e30;
   double x = 0.0;
-  if (fp32_ok) x = (double)newton_h32((float)hi, (float)B, (float)hP, (float)tau, (float)a1, (float)tb);
+  // FP64 polish: from an FP32 root (relative error ~1e-7) one Newton step
+  // leaves ~1e-14; another step is taken only if the first moved by more than
+  // 2e-7 relative (an FP32 root spoiled by cancellation) or there was no FP32 root.
+  double stop = 2e-7;
+  if (fp32_ok) {
+    x = (double)newton_h32((float)hi, (float)B, (float)hP, (float)tau, (float)a1, (float)tb);
+  } else {
+    stop = 1e-8;
+  }
   for (int it = 0; it < 100; ++it) {
     const double t = x + tau;
     const double it1 = fp32_ok ? rcp64(t) : 1.0 / t;
@@ -95,7 +105,8 @@ __device__ __forceinline__ void prox_cell(double mbar, const double (&wbar)[NW],
     if (!(xn >= lo && xn <= hi)) xn = 0.5 * (lo + hi);
     const double dxv = fabs(xn - x);
     x = xn;
-    if (dxv <= 1e-8 * x || hi - lo <= 4e-16 * hi) break;
+    if (dxv <= stop * x || hi - lo <= 4e-16 * hi) break;
+    stop = 1e-8;
   }
   m = x;
   const double s = x * (fp32_ok ? rcp64(x + tau) : 1.0 / (x + tau));
@@ -132,7 +143,8 @@ __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const dou
     const int jm = hmy ? (j == 0 ? g.ny - 1 : j - 1) : j;
     const int jp = hpy ? (j == g.ny - 1 ? 0 : j + 1) : j;
     const double zjm = z[rowi + jm], zjp = z[rowi + jp];
-    double Kz = g.ay * ((hmy ? zc - zjm : 0.0) + (hpy ? zc - zjp : 0.0));
+    // K z: cK z - ay (zN + zS) - ax (zW + zE) away from Neumann ends (fewer FP64 ops)
+    double Kz;
     double xw[NW];
     if (ACTX) {
       const bool per_x = g.perx;
@@ -140,17 +152,22 @@ __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const dou
       const int im = hmx ? (i == 0 ? g.nx - 1 : i - 1) : i;
       const int ip = hpx ? (i == g.nx - 1 ? 0 : i + 1) : i;
       const double zim = z[base + (long long)im * g.ny + j], zip = z[base + (long long)ip * g.ny + j];
-      Kz += g.ax * ((hmx ? zc - zim : 0.0) + (hpx ? zc - zip : 0.0));
+      if (hmx && hpx && hmy && hpy)
+        Kz = fma(2.0 * (g.ax + g.ay), zc, -fma(g.ax, zim + zip, g.ay * (zjm + zjp)));
+      else
+        Kz = g.ay * ((hmy ? zc - zjm : 0.0) + (hpy ? zc - zjp : 0.0)) +
+             g.ax * ((hmx ? zc - zim : 0.0) + (hpx ? zc - zip : 0.0));
       xw[0] = hpx ? (zc - zip) * g.idx : 0.0;
       xw[1] = hmx ? (zim - zc) * g.idx : 0.0;
       xw[2] = hpy ? (zc - zjp) * g.idy : 0.0;
       xw[3] = hmy ? (zjm - zc) * g.idy : 0.0;
     } else {
+      Kz = g.ay * ((hmy ? zc - zjm : 0.0) + (hpy ? zc - zjp : 0.0));
       xw[0] = hpy ? (zc - zjp) * g.idy : 0.0;
       xw[1] = hmy ? (zjm - zc) * g.idy : 0.0;
     }
     const double zn = (k + 1 < g.nt) ? z[e + g.S] : 0.0;
-    const double xm = g.nu * Kz + (zc - zn) * g.idt;
+    const double xm = fma(g.nu, Kz, (zc - zn) * g.idt);
     // prox of y - tau x
     const double m_old = y[e];
     double w_old[NW], wbar[NW], w_new[NW];

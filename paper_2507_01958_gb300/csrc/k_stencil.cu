@@ -189,13 +189,22 @@ void launch_apply_Ct(const Geom& g, const double* p, double* x, cudaStream_t s) 
 // A block owns a TI x TJ spatial tile; p planes are staged in shared memory
 // with a 2-point halo, xm with a 1-point halo.  Each p plane is read from
 // global memory once per tile (plus halo) instead of once per stencil point.
-constexpr int TI = 8, TJ = 32;
+//
+// FP64 issue is the limit on GB300 (1/58 of the FP32 rate), so the stencil is
+// branch-free with the fewest FP64 instructions:
+//   K u = cK u - ax (uW + uE) - ay (uN + uS),   cK = 2 (ax + ay),
+// (5 FP64 ops; nu folded into the coefficients where only nu K u is needed).
+// On a Neumann axis the halos hold mirror images (u_{-1} = u_0, u_N = u_{N-1}),
+// which turns the same formula into the one-sided D^1 (D^1)^T rows of Sec. 4.3;
+// xm halo slots outside the domain are refreshed from their mirrors after xm is
+// formed.
+constexpr int TI = 16, TJ = 32;
 constexpr int H2I = TI + 4, H2J = TJ + 4;  // p tile with halo 2
 constexpr int H1I = TI + 2, H1J = TJ + 2;  // xm tile with halo 1
 
 int aat_chunk(const Geom& g) {
   const long long tiles = (long long)((g.ny + TJ - 1) / TJ) * ((g.nx + TI - 1) / TI);
-  long long want = 152 * 8;
+  long long want = 152 * 4;
   long long chunks = (want + tiles - 1) / tiles;
   if (chunks < 1) chunks = 1;
   if (chunks > g.nt) chunks = g.nt;
@@ -210,6 +219,18 @@ int aat_blocks(const Geom& g) {
   return ((g.ny + TJ - 1) / TJ) * ((g.nx + TI - 1) / TI) * ((g.nt + kc - 1) / kc);
 }
 
+// Index of grid point i on an axis: wrapped when periodic, mirrored across the
+// end when Neumann (i = -1 -> 0, -2 -> 1, N -> N-1, N+1 -> N-2).
+__device__ __forceinline__ int halo_index(int i, int N, int per) {
+  if (i >= 0 && i < N) return i;
+  if (per) {
+    i %= N;
+    return i < 0 ? i + N : i;
+  }
+  int m = i < 0 ? -1 - i : 2 * N - 1 - i;
+  return m < 0 ? 0 : (m >= N ? N - 1 : m);
+}
+
 __device__ __forceinline__ void load_plane_h2(const Geom& g, const double* __restrict__ p, int k,
                                               int i0, int j0, double (*dst)[H2J]) {
   const int tid = threadIdx.x + TJ * threadIdx.y;
@@ -220,16 +241,24 @@ __device__ __forceinline__ void load_plane_h2(const Geom& g, const double* __res
   const double* pk = p + (long long)k * g.S;
   for (int s = tid; s < H2I * H2J; s += TI * TJ) {
     const int li = s / H2J, lj = s % H2J;
-    const int gi = wrap_or_neg(i0 + li - 2, g.nx, g.perx);
-    const int gj = wrap_or_neg(j0 + lj - 2, g.ny, g.pery);
-    dst[li][lj] = (gi >= 0 && gj >= 0) ? pk[(long long)gi * g.ny + gj] : 0.0;
+    const int gi = halo_index(i0 + li - 2, g.nx, g.perx);
+    const int gj = halo_index(j0 + lj - 2, g.ny, g.pery);
+    dst[li][lj] = pk[(long long)gi * g.ny + gj];
   }
 }
 
+template <int ACTX, int WID>
+__device__ __forceinline__ double fast_K(const double (*A)[WID], int r, int c, double ax, double ay,
+                                         double cK) {
+  double t = ay * (A[r][c - 1] + A[r][c + 1]);
+  if (ACTX) t = fma(ax, A[r - 1][c] + A[r + 1][c], t);
+  return fma(cK, A[r][c], -t);
+}
+
 template <int ACTX>
-__global__ void __launch_bounds__(TI * TJ) k_AAt(Geom g, int kc, const double* __restrict__ p,
-                                                 double* __restrict__ q, double* partials,
-                                                 DevScalars* sc, int mode) {
+__global__ void __launch_bounds__(TI * TJ, 2) k_AAt(Geom g, int kc, const double* __restrict__ p,
+                                                    double* __restrict__ q, double* partials,
+                                                    DevScalars* sc, int mode) {
   if (mode == 1 && sc->cg_done) return;
   __shared__ double P[2][H2I][H2J];
   __shared__ double XM[H1I][H1J];
@@ -240,26 +269,13 @@ __global__ void __launch_bounds__(TI * TJ) k_AAt(Geom g, int kc, const double* _
   const int k1 = min(g.nt, k0 + kc);
   const int gi = i0 + ti, gj = j0 + tj;
   const bool own = gi < g.nx && gj < g.ny;
-  const double nax = g.nu * g.ax, nay = g.nu * g.ay;
-
-  // Neighbour masks of one halo-1 slot (global point (i0+li-1, j0+lj-1)).
-  auto xm_at = [&](double (*Pk)[H2J], double (*Pk1)[H2J], int li, int lj, double* kp_out) -> double {
-    const int xi = i0 + li - 1, xj = j0 + lj - 1;
-    const int hi = li + 1, hj = lj + 1;  // same point in the halo-2 tile
-    const double c = Pk[hi][hj];
-    bool hm, hp;
-    if (g.pery) { hm = hp = true; } else { hm = xj >= 1; hp = xj <= g.ny - 2; }
-    double Ky = (hm ? c - Pk[hi][hj - 1] : 0.0) + (hp ? c - Pk[hi][hj + 1] : 0.0);
-    double Kx = 0.0;
-    if (ACTX) {
-      bool xm_, xp_;
-      if (g.perx) { xm_ = xp_ = true; } else { xm_ = xi >= 1; xp_ = xi <= g.nx - 2; }
-      Kx = (xm_ ? c - Pk[hi - 1][hj] : 0.0) + (xp_ ? c - Pk[hi + 1][hj] : 0.0);
-    }
-    const double kp = g.ax * Kx + g.ay * Ky;
-    if (kp_out) *kp_out = kp;
-    return g.nu * kp + (c - Pk1[hi][hj]) * g.idt;
-  };
+  const double ax = ACTX ? g.ax : 0.0, ay = g.ay, cK = 2.0 * (ax + ay);
+  const double nax = g.nu * ax, nay = g.nu * ay, ncK = g.nu * cK;
+  // xm halo slots that lie outside a Neumann axis (rebuilt from their mirrors)
+  const bool ghost_x = ACTX && !g.perx && (i0 == 0 || i0 + TI >= g.nx);
+  const bool ghost_y = !g.pery && (j0 == 0 || j0 + TJ >= g.ny);
+  const bool ghosts = ghost_x || ghost_y;
+  const int tid = tj + TJ * ti;
 
   int cur = 0;
   load_plane_h2(g, p, k0, i0, j0, P[cur]);
@@ -267,38 +283,48 @@ __global__ void __launch_bounds__(TI * TJ) k_AAt(Geom g, int kc, const double* _
   if (k0 > 0) {
     load_plane_h2(g, p, k0 - 1, i0, j0, P[cur ^ 1]);
     __syncthreads();
-    if (own) xprev = xm_at(P[cur ^ 1], P[cur], ti + 1, tj + 1, nullptr);
+    if (own)
+      xprev = fast_K<ACTX, H2J>(P[cur ^ 1], ti + 2, tj + 2, nax, nay, ncK) +
+              (P[cur ^ 1][ti + 2][tj + 2] - P[cur][ti + 2][tj + 2]) * g.idt;
     __syncthreads();
   }
   double acc = 0.0;
-  const int tid = tj + TJ * ti;
   for (int k = k0; k < k1; ++k) {
     load_plane_h2(g, p, k + 1, i0, j0, P[cur ^ 1]);
     __syncthreads();
+    const double (*Pk)[H2J] = P[cur];
+    const double (*Pn)[H2J] = P[cur ^ 1];
+    // One FP64 sequence for every slot (no divergent paths): K p, then xm.
     for (int s = tid; s < H1I * H1J; s += TI * TJ) {
       const int li = s / H1J, lj = s % H1J;
-      const bool inner = li >= 1 && li <= TI && lj >= 1 && lj <= TJ;
-      double kp;
-      XM[li][lj] = xm_at(P[cur], P[cur ^ 1], li, lj, inner ? &kp : nullptr);
-      if (inner) KP[li - 1][lj - 1] = kp;
+      const double kp = fast_K<ACTX, H2J>(Pk, li + 1, lj + 1, ax, ay, cK);
+      XM[li][lj] = fma(g.nu, kp, (Pk[li + 1][lj + 1] - Pn[li + 1][lj + 1]) * g.idt);
+      if (li >= 1 && li <= TI && lj >= 1 && lj <= TJ) KP[li - 1][lj - 1] = kp;
     }
     __syncthreads();
+    if (ghosts) {
+      for (int s = tid; s < H1I * H1J; s += TI * TJ) {
+        const int li = s / H1J, lj = s % H1J;
+        const int xi = i0 + li - 1, xj = j0 + lj - 1;
+        const bool ox = ghost_x && (xi < 0 || xi >= g.nx);
+        const bool oy = ghost_y && (xj < 0 || xj >= g.ny);
+        if (ox || oy) {
+          const int mi = ox ? (xi < 0 ? li + 1 : li - 1) : li;
+          const int mj = oy ? (xj < 0 ? lj + 1 : lj - 1) : lj;
+          // mirror slot is inside the domain (read-only here: distinct from ghosts)
+          XM[li][lj] = XM[mi][mj];
+        }
+      }
+      __syncthreads();
+    }
     if (own) {
       const double c = XM[ti + 1][tj + 1];
-      bool hm, hp;
-      if (g.pery) { hm = hp = true; } else { hm = gj >= 1; hp = gj <= g.ny - 2; }
-      double Ky = (hm ? c - XM[ti + 1][tj] : 0.0) + (hp ? c - XM[ti + 1][tj + 2] : 0.0);
-      double Kx = 0.0;
-      if (ACTX) {
-        bool xm_, xp_;
-        if (g.perx) { xm_ = xp_ = true; } else { xm_ = gi >= 1; xp_ = gi <= g.nx - 2; }
-        Kx = (xm_ ? c - XM[ti][tj + 1] : 0.0) + (xp_ ? c - XM[ti + 2][tj + 1] : 0.0);
-      }
-      const double val = nax * Kx + nay * Ky + (c - xprev) * g.idt + 2.0 * KP[ti][tj];
+      const double nKxm = fast_K<ACTX, H1J>(XM, ti + 1, tj + 1, nax, nay, ncK);
+      const double val = fma(2.0, KP[ti][tj], fma(c - xprev, g.idt, nKxm));
       xprev = c;
       const long long e = (long long)k * g.S + (long long)gi * g.ny + gj;
       q[e] = val;
-      acc += val * P[cur][ti + 2][tj + 2];
+      acc = fma(val, Pk[ti + 2][tj + 2], acc);
     }
     __syncthreads();
     cur ^= 1;

@@ -173,7 +173,9 @@ int check_b(mfg_plan_t pl, int b) {
   return MFG_OK;
 }
 
-int launches_per_iter(const Inst& in) { return 4 + precond_kernel_count(in.g); }
+// kernels per CP iteration outside PCG (rhs, precond, init_p, arm, prox) and per PCG iteration
+int launches_cp(const Inst& in) { return 4 + precond_kernel_count(in.g); }
+int launches_cg(const Inst& in) { return 3 + precond_dot_kernel_count(in.g, in.tabs); }
 
 // Captures the per-instance CP loop into `top` as a while-node branch.
 int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, const double* V,
@@ -216,10 +218,10 @@ int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, con
 
   cudaStream_t s2 = pl->cap1;
   CK(cudaStreamBeginCaptureToGraph(s2, body_cg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  const PcgDot dot{in.r, in.q, in.partials, in.sc, flex};
   launch_AAt(g, in.pv, in.q, in.partials, in.sc, 1, s2);
   launch_update_zr(g.n, z, in.r, in.pv, in.q, in.partials, in.sc, s2);
-  launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s2);
-  launch_dot_beta(g.n, in.r, in.zp, in.q, flex, in.partials, in.sc, s2);
+  launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s2, &dot);
   launch_update_p(g.n, in.zp, in.pv, in.sc, hg, 1, s2);
   CK(cudaStreamEndCapture(s2, &body_cg));
   return MFG_OK;
@@ -271,12 +273,12 @@ int solve_eager(mfg_plan_t pl, const double* m0, const double* V, const double* 
         CK(cudaMemcpyAsync(&hs, in.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (hs.cg_done) break;
+        const PcgDot dot{in.r, in.q, in.partials, in.sc, flex};
         launch_AAt(g, in.pv, in.q, in.partials, in.sc, 1, s);
         launch_update_zr(g.n, zb, in.r, in.pv, in.q, in.partials, in.sc, s);
-        launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s);
-        launch_dot_beta(g.n, in.r, in.zp, in.q, flex, in.partials, in.sc, s);
+        launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s, &dot);
         launch_update_p(g.n, in.zp, in.pv, in.sc, 0, 0, s);
-        pl->launches += 4 + precond_kernel_count(g);
+        pl->launches += 3 + precond_dot_kernel_count(g, in.tabs);
       }
       launch_prox_cp(g, in.cf, zb, yb, ybb, Vb, Wb, in.partials, in.sc, 0, 0, s);
       pl->launches += 1;
@@ -338,7 +340,8 @@ int mfg_plan(const mfg_problem* probs, int batch, mfg_plan_t* out) {
     int rc = build_prec_tables(in.p, in.g, &in.tabs, &err);
     if (rc != MFG_OK) return bail(rc, err);
     const size_t n = (size_t)in.g.n;
-    size_t npart = (size_t)std::max(2 * kRedBlocks, aat_blocks(in.g));
+    size_t npart = (size_t)std::max<long long>(std::max(2 * kRedBlocks, aat_blocks(in.g)),
+                                               fft_dot_partials(in.g));
     if (cudaMalloc(&in.r, n * 8) != cudaSuccess || cudaMalloc(&in.pv, n * 8) != cudaSuccess ||
         cudaMalloc(&in.q, n * 8) != cudaSuccess || cudaMalloc(&in.zp, n * 8) != cudaSuccess ||
         cudaMalloc(&in.partials, npart * 8) != cudaSuccess)
@@ -460,7 +463,8 @@ int mfg_solve(mfg_plan_t pl, const double* m0, const double* V, const double* W,
     st[b].r_last = h.r_last;
     st[b].tau = h.tau;
     st[b].sigma = h.sigma;
-    if (!eager) pl->launches += (long long)launches_per_iter(pl->inst[b]) * (h.cp_iters + h.cg_total);
+    if (!eager)
+      pl->launches += (long long)launches_cp(pl->inst[b]) * h.cp_iters + (long long)launches_cg(pl->inst[b]) * h.cg_total;
     if (first == MFG_OK && h.status != MFG_OK) first = h.status;
   }
   if (first != MFG_OK) return fail(first, "an instance finished with a non-OK status");
@@ -530,13 +534,13 @@ int mfg_adjoint(mfg_plan_t pl, int b, const double* y, const double* z, const do
     CK(cudaMemcpyAsync(&hs, in.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (hs.cg_done) break;
+    const PcgDot dot{in.r, in.q, in.partials, in.sc, flex};
     launch_ct_hinv(g, in.cf, y, in.pv, nullptr, in.adj_t, s, in.sc);
     launch_apply_C(g, in.adj_t, in.q, 1.0, nullptr, in.partials, in.sc, 2, s, in.pv);
     launch_update_zr(g.n, in.adj_eta, in.r, in.pv, in.q, in.partials, in.sc, s);
-    launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s);
-    launch_dot_beta(g.n, in.r, in.zp, in.q, flex, in.partials, in.sc, s);
+    launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s, &dot);
     launch_update_p(g.n, in.zp, in.pv, in.sc, 0, 0, s);
-    launches += 5 + precond_kernel_count(g);
+    launches += 4 + precond_dot_kernel_count(g, in.tabs);
   }
   // mu = H^{-1}(g - C^T eta), then the contractions
   launch_ct_hinv(g, in.cf, y, in.adj_eta, gy, in.adj_t, s, nullptr);

@@ -10,7 +10,9 @@
 namespace mfg {
 
 constexpr int kThreads = 256;        // threads per block for 1-D launches
-constexpr int kRedBlocks = 152 * 4;  // fixed grid of the grid-stride reduction kernels
+// Fixed grid of the grid-stride reduction kernels.  Kept small: every thread
+// pays a warp-shuffle tree of FP64 adds at the end, and FP64 issue is scarce.
+constexpr int kRedBlocks = 152 * 2;
 constexpr int kMaxNt = 256;          // largest N_t of the fused time-transform kernel
 
 // Geometry and coefficients of one instance on the device.  Internally every
@@ -100,21 +102,35 @@ struct PrecTables {
 };
 int build_prec_tables(const mfg_problem& p, const Geom& g, PrecTables* t, std::string* err);
 void free_prec_tables(PrecTables* t);
+// Operands of the PCG dot products that the last preconditioner pass can fuse
+// (r.zp and, for the flexible variant, q.zp, then beta).
+struct PcgDot {
+  const double* r;
+  const double* q;
+  double* partials;
+  DevScalars* sc;
+  int flex;
+};
 // z = P^{-1} r.  work64: 2n doubles (FP64 path); work32: 2n floats (mixed path).
+// With dot != nullptr the PCG dot products and beta are formed as well (fused
+// into the last pass when it is an FFT pass, else by k_dot_beta).
 void launch_precond(const Geom& g, const PrecTables& t, int precision, const double* r, double* z,
-                    double* work64, float* work32, const DevScalars* sc, cudaStream_t s);
+                    double* work64, float* work32, const DevScalars* sc, cudaStream_t s,
+                    const PcgDot* dot = nullptr);
 int precond_kernel_count(const Geom& g);
+int precond_dot_kernel_count(const Geom& g, const PrecTables& t);
 int precond_configure();
 
 // FFT spatial passes (k_fft.cu).
 bool fft_supported(int N);
+long long fft_dot_partials(const Geom& g);
 int fft_configure();
 template <typename T>
 void fft_y_forward(int N, int periodic, const double* in, T* out, const T* tw, const T* dct,
                    long long nlines, const DevScalars* sc, cudaStream_t s);
 template <typename T>
 void fft_y_inverse(int N, int periodic, const T* in, double* out, const T* tw, const T* dct,
-                   long long nlines, const DevScalars* sc, cudaStream_t s);
+                   long long nlines, const DevScalars* sc, cudaStream_t s, const PcgDot* dot);
 template <typename T>
 void fft_x(int N, int periodic, int inverse, const T* in, T* out, const T* tw, const T* dct,
            long long inner, long long outer, const DevScalars* sc, cudaStream_t s);
