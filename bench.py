@@ -143,6 +143,93 @@ AAT_FLOPS_PER_UNKNOWN = 27
 FP64_PEAK_TFLOPS = 1.25
 
 
+def profiled_traffic(name):
+    """DRAM bytes per launch (read + write) recorded by the ncu summary in
+    profiles/<name> ("dram_bytes_per_launch: X"), or None."""
+    import re
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", open(path).read())
+    return float(m.group(1)) if m else None
+
+
+def adjoint_measure(dev, cp_iters=300):
+    """One forward solve (mixed, 300 CP iterations) and one adjoint solve on the
+    128^2 x 64 periodic workload with nu = 0.05 (loss on m(T)); returns timings."""
+    import torch
+    import paper_2507_01958_gb300 as pkg
+    L = pkg.lib()
+    inst = mi.config4()
+    p = dict(inst["problem"], max_cp=cp_iters, cg_tol=CG_TOL, precision="mixed")
+    plan = L.mfg_plan(p)
+    n = p["nt"] * p["n"][0] * p["n"][1]
+    S = p["n"][0] * p["n"][1]
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).reshape(-1).to(dev)
+    y = t(inst["y0"])
+    ybar = y.clone()
+    z = torch.zeros(n, dtype=torch.float64, device=dev)
+    L.mfg_solve(plan, t(inst["m0"]), t(inst["V"]), t(inst["W"]), y, ybar, z)
+    dx = p["len"][0] / p["n"][0]
+    gy = torch.zeros_like(y)
+    gy[(p["nt"] - 1) * S: p["nt"] * S] = 2.0 * (y[(p["nt"] - 1) * S: p["nt"] * S] - t(inst["m_target"])) * dx * dx
+    out = [torch.empty(S, dtype=torch.float64, device=dev) for _ in range(3)]
+    dnu = torch.empty(1, dtype=torch.float64, device=dev)
+    L.mfg_adjoint(plan, 0, y, z, gy, out[0], out[1], out[2], dnu, tol=1e-10)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, st = L.mfg_adjoint(plan, 0, y, z, gy, out[0], out[1], out[2], dnu, tol=1e-10)
+    torch.cuda.synchronize()
+    return {"workload": "2-D periodic 128x128, N_t=64, nu=0.05, loss ||m(T)-m_target||^2",
+            "ms": 1e3 * (time.perf_counter() - t0), "adjoint_pcg_iters": int(st.cg_iters),
+            "final_rel_residual": st.r_last, "status": int(rc), "dnu": float(dnu.item())}
+
+
+def batch_measure(dev, count=64, cp_iters=20):  # noqa: C901
+    """The uneven batch: `count` seeded instances (periodic or Neumann, N in
+    {64,128,256}, N_t in {32,64,128}, nu log-uniform) in one plan and one graph
+    launch; returns aggregate CP iterations/s."""
+    import torch
+    import paper_2507_01958_gb300 as pkg
+    L = pkg.lib()
+    insts = mi.config5(count=count, with_y0=False)
+    probs = [dict(i["problem"], max_cp=cp_iters, cg_tol=CG_TOL, precision="mixed") for i in insts]
+    plan = L.mfg_plan(probs)
+    sz = L.mfg_sizes(plan)
+
+    def pack(key, total, part):
+        buf = torch.zeros(total, dtype=torch.float64, device=dev)
+        for b, i in enumerate(insts):
+            off = L.mfg_layout(plan, b)[part]
+            a = torch.as_tensor(np.ascontiguousarray(i[key], dtype=np.float64)).reshape(-1)
+            buf[off: off + a.numel()] = a.to(dev)
+        return buf
+
+    m0, V, W = (pack(k, sz["field"], "field_off") for k in ("m0", "V", "W"))
+    # start m^k = m0 for every k, w = 0, built on the device from m0
+    y0 = torch.zeros(sz["primal"], dtype=torch.float64, device=dev)
+    for b, i in enumerate(insts):
+        lay = L.mfg_layout(plan, b)
+        S = lay["n"] // i["problem"]["nt"]
+        f0, p0 = lay["field_off"], lay["primal_off"]
+        y0[p0: p0 + lay["n"]] = m0[f0: f0 + S].repeat(i["problem"]["nt"])
+    y, ybar = y0.clone(), y0.clone()
+    z = torch.zeros(sz["dual"], dtype=torch.float64, device=dev)
+    L.mfg_solve(plan, m0, V, W, y, ybar, z)  # warm-up (graph build)
+    y.copy_(y0); ybar.copy_(y0); z.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, st = L.mfg_solve(plan, m0, V, W, y, ybar, z)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    cp = sum(s.cp_iters for s in st)
+    nsum = sum(i["problem"]["nt"] * i["problem"]["n"][0] * i["problem"]["n"][1] for i in insts)
+    return {"workload": f"{count} uneven instances (seeds 100..{100 + count - 1}), {cp_iters} CP iterations each",
+            "cp_iters_per_s": cp / el, "unknowns_total": nsum,
+            "unknowns_cp_iters_per_s": nsum * cp_iters / el, "seconds": el,
+            "pcg_iters": int(sum(s.cg_iters for s in st)), "status_ok": all(s.status == 0 for s in st)}
+
+
 def build_batch(precision, cp_per_step=CP_PER_STEP):
     insts = [mi.config2(nu=nu) for nu in NUS]
     probs = []
@@ -263,11 +350,7 @@ def run_gpu(args):
     t_aat = a0.elapsed_time(a1) / 1e3 / reps
     flops = AAT_FLOPS_PER_UNKNOWN * n_per
     achieved = flops / t_aat / 1e12
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "k_AAt_traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            traffic = json.load(f).get("bytes_per_launch")
+    traffic = profiled_traffic("k_AAt_config2.md")
 
     # End to end through the host-buffer entry point (copies inside the timed region).
     pin = lambda a: torch.as_tensor(a).pin_memory()
@@ -287,6 +370,9 @@ def run_gpu(args):
     cp_e2e = reduce_sum(float(sum(s.cp_iters for s in st) * e2e_steps), world, dev)
     h2d = 8 * (3 * sz["field"] + 2 * sz["primal"] + sz["dual"])
     d2h = 8 * (2 * sz["primal"] + sz["dual"])
+
+    adj = adjoint_measure(dev) if not args.no_extras else None
+    batch = batch_measure(dev) if not args.no_extras else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -328,12 +414,40 @@ def run_gpu(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk,
+            "adjoint": adj,
+            "batch_uneven": batch,
         }
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as td
         td.barrier()
         td.destroy_process_group()
+
+
+def run_kernels_only(args):
+    """Three launches each of the standalone AAt, preconditioner and prox entry
+    points on one instance of the workload (a short program for ncu captures)."""
+    import torch
+    import paper_2507_01958_gb300 as pkg
+    L = pkg.lib()
+    insts, probs = build_batch(args.precision, 1)
+    inst, p = insts[1], probs[1]
+    plan = L.mfg_plan(p)
+    n = p["nt"] * p["n"][0] * p["n"][1]
+    g = torch.Generator(device="cuda").manual_seed(0)
+    r = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+    z = torch.empty_like(r)
+    v = torch.randn(5 * n, dtype=torch.float64, device="cuda", generator=g)
+    v[:n] += 2.0
+    y = torch.empty_like(v)
+    V = torch.as_tensor(inst["V"]).reshape(-1).cuda()
+    W = torch.zeros_like(V)
+    for _ in range(3):
+        L.mfg_apply_AAt(plan, 0, r, z)
+        L.mfg_apply_precond(plan, 0, r, z)
+        L.mfg_prox(plan, 0, 0.5, v, V, W, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernels_only": True, "unknowns": n, "launches": L.mfg_kernel_launches(plan)}))
 
 
 def cpu_baseline_sample(seconds=15.0, steps=None):
@@ -404,11 +518,16 @@ def main(argv=None):
     ap.add_argument("--cp-per-step", type=int, default=CP_PER_STEP)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--quick", action="store_true", help="main timed loop only (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and uneven-batch lines")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="three launches of each standalone hot kernel (for ncu captures)")
     ap.add_argument("--eager", action="store_true",
                     help="issue kernels one by one instead of one graph launch (per-kernel profiling)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.kernels_only:
+        run_kernels_only(args)
     else:
         run_gpu(args)
 

@@ -189,7 +189,7 @@ def config4(n=128, nt=64):
     return _inst(prob, m0, V, W, initial_iterate(prob, m0), m_target=mt, v_modes=vinfo)
 
 
-def config5_instance(seed, sizes=(64, 128, 256), nts=(32, 64, 128)):
+def config5_instance(seed, sizes=(64, 128, 256), nts=(32, 64, 128), with_y0=True):
     """One instance of the uneven batch: bc ~ U{periodic, Neumann}, N ~ U(sizes),
     N_t ~ U(nts), nu = 10^U(-3, 0); V, m0 as config2 (cosine series for Neumann)."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -204,7 +204,7 @@ def config5_instance(seed, sizes=(64, 128, 256), nts=(32, 64, 128)):
         V = cosine_potential(prob, rng)
     m0 = gaussian_mixture(prob, rng, images=2 if bc == PERIODIC else 0)
     W = np.zeros_like(V)
-    return _inst(prob, m0, V, W, initial_iterate(prob, m0))
+    return _inst(prob, m0, V, W, initial_iterate(prob, m0) if with_y0 else None)
 
 
 def config5(count=64, first_seed=100, **kw):

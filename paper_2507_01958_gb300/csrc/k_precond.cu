@@ -404,67 +404,74 @@ __global__ void __launch_bounds__(256) k_time_fast(const T* __restrict__ in, T* 
   using Sh = TimeShape<T, NT>;
   constexpr int TW = Sh::TW, RN = Sh::RN, CG = Sh::CG, RM = Sh::RM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Vs = reinterpret_cast<T*>(smem_raw);  // [NT][NT]
+  T* Vs = reinterpret_cast<T*>(smem_raw);  // [NT][NT], loaded once per block
   T* X = Vs + NT * NT;                      // [NT][TW]
   const int tid = threadIdx.x;
   const int cg = tid % CG, rg = tid / CG;
   const int r0 = rg * RM;  // this thread's rows r0 .. r0 + RM - 1
-  const int s0 = blockIdx.x * TW;
   for (int q = tid; q < NT * NT; q += 256) Vs[q] = V[q];
-  for (int q = tid; q < NT * TW; q += 256) {
-    const int k = q / TW, c = q % TW;
-    X[q] = (s0 + c < S) ? in[(long long)k * S + s0 + c] : T(0);
-  }
-  __syncthreads();
-  T acc[RM][RN];
+  T lam[RM];
 #pragma unroll
-  for (int u = 0; u < RM; ++u)
-#pragma unroll
-    for (int v = 0; v < RN; ++v) acc[u][v] = T(0);
-  // Y = V X: row r uses V[r][b] = V[b][r] (symmetric V), contiguous in r
-#pragma unroll 4
-  for (int b = 0; b < NT; ++b) {
-    T xv[RN], vv[RM];
-    lds_vec<RN>(X + b * TW + cg * RN, xv);
-    lds_vec<RM>(Vs + b * NT + r0, vv);
+  for (int u = 0; u < RM; ++u) lam[u] = lamt[r0 + u];
+  const int nstrips = (S + TW - 1) / TW;
+  // the block walks strips of TW spatial modes, reusing V from shared memory
+  for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x) {
+    const int s0 = strip * TW;
+    __syncthreads();  // previous strip done with X (and V loaded on the first pass)
+    for (int q = tid; q < NT * TW; q += 256) {
+      const int k = q / TW, c = q % TW;
+      X[q] = (s0 + c < S) ? in[(long long)k * S + s0 + c] : T(0);
+    }
+    __syncthreads();
+    T acc[RM][RN];
 #pragma unroll
     for (int u = 0; u < RM; ++u)
 #pragma unroll
-      for (int v = 0; v < RN; ++v) acc[u][v] = fma(vv[u], xv[v], acc[u][v]);
-  }
-  __syncthreads();
-  // divide by S(k, s) = Lambda_1(s) + lambda_k Lambda_2(s); Y overwrites X
+      for (int v = 0; v < RN; ++v) acc[u][v] = T(0);
+    // Y = V X: row r uses V[r][b] = V[b][r] (symmetric V), contiguous in r
+#pragma unroll 4
+    for (int b = 0; b < NT; ++b) {
+      T xv[RN], vv[RM];
+      lds_vec<RN>(X + b * TW + cg * RN, xv);
+      lds_vec<RM>(Vs + b * NT + r0, vv);
 #pragma unroll
-  for (int v = 0; v < RN; ++v) {
-    const int c = cg * RN + v;
-    const int s = s0 + c;
-    const T l1 = s < S ? L1[s] : T(1), l2 = s < S ? L2[s] : T(0);
+      for (int u = 0; u < RM; ++u)
+#pragma unroll
+        for (int v = 0; v < RN; ++v) acc[u][v] = fma(vv[u], xv[v], acc[u][v]);
+    }
+    __syncthreads();
+    // divide by S(k, s) = Lambda_1(s) + lambda_k Lambda_2(s); Y overwrites X
+#pragma unroll
+    for (int v = 0; v < RN; ++v) {
+      const int c = cg * RN + v;
+      const int s = s0 + c;
+      const T l1 = s < S ? L1[s] : T(1), l2 = s < S ? L2[s] : T(0);
+#pragma unroll
+      for (int u = 0; u < RM; ++u) {
+        X[(r0 + u) * TW + c] = acc[u][v] / (l1 + lam[u] * l2);
+        acc[u][v] = T(0);
+      }
+    }
+    __syncthreads();
+    // out = V^T Y: out[a][c] = sum_b V[b][a] Y[b][c]
+#pragma unroll 4
+    for (int b = 0; b < NT; ++b) {
+      T yv[RN], vv[RM];
+      lds_vec<RN>(X + b * TW + cg * RN, yv);
+      lds_vec<RM>(Vs + b * NT + r0, vv);
+#pragma unroll
+      for (int u = 0; u < RM; ++u)
+#pragma unroll
+        for (int v = 0; v < RN; ++v) acc[u][v] = fma(vv[u], yv[v], acc[u][v]);
+    }
 #pragma unroll
     for (int u = 0; u < RM; ++u) {
       const int r = r0 + u;
-      X[r * TW + c] = acc[u][v] / (l1 + lamt[r] * l2);
-      acc[u][v] = T(0);
-    }
-  }
-  __syncthreads();
-  // out = V^T Y: out[a][c] = sum_b V[b][a] Y[b][c]
-#pragma unroll 4
-  for (int b = 0; b < NT; ++b) {
-    T yv[RN], vv[RM];
-    lds_vec<RN>(X + b * TW + cg * RN, yv);
-    lds_vec<RM>(Vs + b * NT + r0, vv);
 #pragma unroll
-    for (int u = 0; u < RM; ++u)
-#pragma unroll
-      for (int v = 0; v < RN; ++v) acc[u][v] = fma(vv[u], yv[v], acc[u][v]);
-  }
-#pragma unroll
-  for (int u = 0; u < RM; ++u) {
-    const int r = r0 + u;
-#pragma unroll
-    for (int v = 0; v < RN; ++v) {
-      const int s = s0 + cg * RN + v;
-      if (s < S) out[(long long)r * S + s] = acc[u][v];
+      for (int v = 0; v < RN; ++v) {
+        const int s = s0 + cg * RN + v;
+        if (s < S) out[(long long)r * S + s] = acc[u][v];
+      }
     }
   }
 }
@@ -473,7 +480,10 @@ template <typename T, int NT>
 static void launch_time_fast(const T* in, T* out, const T* V, const T* lamt, const T* L1, const T* L2,
                              int S, const DevScalars* sc, cudaStream_t s) {
   using Sh = TimeShape<T, NT>;
-  k_time_fast<T, NT><<<(S + Sh::TW - 1) / Sh::TW, 256, Sh::smem, s>>>(in, out, V, lamt, L1, L2, S, sc);
+  // enough blocks to fill the GPU (several resident per SM); each walks strips
+  const int nstrips = (S + Sh::TW - 1) / Sh::TW;
+  const int blocks = nstrips < 152 * 4 ? nstrips : 152 * 4;
+  k_time_fast<T, NT><<<blocks, 256, Sh::smem, s>>>(in, out, V, lamt, L1, L2, S, sc);
 }
 
 template <typename T>
