@@ -53,10 +53,17 @@ def h_eq(m, mbar, P2, tau, a, b, c):
 def prox(prob, tau, v, V, W, max_iter=4000):
     """prox_{tau phi}(v) for v of shape (c, nt, Nx, Ny); returns the same shape."""
     v = np.asarray(v, dtype=np.float64)
+    a, b, c = coupling(prob, V, W)
+    return prox_cells(tau, v, a, b, c, max_iter)
+
+
+def prox_cells(tau, v, a, b, c, max_iter=4000):
+    """The same map for any set of cells: v of shape (c, ...) with coefficient
+    arrays a, c of shape v.shape[1:] and scalar b."""
+    v = np.asarray(v, dtype=np.float64)
     mbar = v[0]
     P = project_K(v[1:])
     P2 = (P * P).sum(axis=0)
-    a, b, c = coupling(prob, V, W)
     zero = h_eq(0.0, mbar, P2, tau, a, b, c) >= 0.0
     lo = np.zeros_like(mbar)
     hi = np.maximum(0.0, mbar - tau * c) + P2 / (2.0 * tau)

@@ -148,6 +148,50 @@ def precond_modal(prob, r):
     return np.real(from_modes(prob, zh)).reshape(-1)
 
 
+def tridiag_mult(diag, off, x):
+    """y = T x along axis 0 for a symmetric tridiagonal T with constant off-diagonal."""
+    y = diag * x
+    y[:-1] += off * x[1:]
+    y[1:] += off * x[:-1]
+    return y
+
+
+def _modal_blocks(prob):
+    nt = prob["nt"]
+    kap = laplacian_eigs(prob)
+    h = dt(prob)
+    return nt, kap, h
+
+
+def apply_AAt_modal(prob, p):
+    """AAt p through the spatial eigenbasis (same blocks as solve_AAt_modal,
+    multiplied instead of solved): a matrix-free AAt for grids too large to
+    assemble."""
+    nt, kap, h = _modal_blocks(prob)
+    nx, ny = prob["n"]
+    Ls = prob["nu"] * kap + 1.0 / h
+    Cs = Ls ** 2 + 2.0 * kap
+    diag = np.broadcast_to(Cs, (nt,) + Cs.shape).copy()
+    diag[1:] += 1.0 / h ** 2
+    ph = to_modes(prob, np.asarray(p, dtype=np.float64).reshape(nt, nx, ny))
+    return np.real(from_modes(prob, tridiag_mult(diag, -Ls / h, ph))).reshape(-1)
+
+
+def apply_P_modal(prob, z):
+    """P z for the preconditioner of eq. prec, through the spatial eigenbasis;
+    also returns the largest eigenvalue of P (its 2-norm)."""
+    nt, kap, h = _modal_blocks(prob)
+    nx, ny = prob["n"]
+    Lh = (prob["nu"] * kap + 1.0 / h) / h
+    Ch = prob["nu"] ** 2 * kap ** 2 + 2.0 * kap
+    diag = np.broadcast_to(Ch + 2.0 * Lh, (nt,) + Ch.shape).copy()
+    diag[0] = Ch + prob["l"] * Lh
+    zh = to_modes(prob, np.asarray(z, dtype=np.float64).reshape(nt, nx, ny))
+    out = np.real(from_modes(prob, tridiag_mult(diag, -Lh, zh))).reshape(-1)
+    lam_max = float((Ch + 4.0 * Lh).max())  # Gershgorin bound, attained up to O(1/nt^2)
+    return out, lam_max
+
+
 def pcg(apply_A, apply_Minv, b, tol, x0=None, maxiter=10000):
     """Preconditioned CG (Fletcher-Reeves beta), ||r|| <= tol ||b||; returns (x, it)."""
     x = np.zeros_like(b) if x0 is None else x0.copy()

@@ -208,3 +208,51 @@ def test_config1_fixed_count(precision):
     err = rel(y, ref["y"])
     print(f"config1 {precision}: rel err {err:.3e}, PCG iterations {st.cg_iters}")
     assert err <= 1e-8
+
+
+@pytest.mark.parametrize("case", CASES[:3] + POW2[:1])
+def test_prox_quadratic_coupling(case):
+    """f(x, m) = f_a m + f_b m^2 + V(x) with f_b > 0 (the crowd-aversion coupling
+    of the paper's Problem 1): the prox equation is no longer concave."""
+    import torch
+    inst = _inst(case, f_a=0.0)
+    p = dict(inst["problem"], f_b=0.5)
+    plan = _plan(p)
+    s, n, c = ops.sizes(p)
+    v = mi.random_field((c, p["nt"]) + tuple(p["n"]), 61, -2.0, 2.0)
+    v[0] += 0.5
+    y = torch.empty(c * n, dtype=torch.float64, device="cuda")
+    for tau in (0.05, 1.0, 7.0):
+        lib().mfg_prox(plan, 0, tau, dev(v), dev(inst["V"]), dev(inst["W"]), y)
+        torch.cuda.synchronize()
+        ref = oracle_prox(p, tau, v, inst["V"], inst["W"]).reshape(-1)
+        assert np.abs(host(y) - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+
+
+def test_problem1_shape_adaptive_tolerance():
+    """Problem 1 of Sec. 5.1 on a small grid (16^2, N_t = 32): f = (m^2 - sin 2 pi y
+    - sin 2 pi x - cos 4 pi x)/2, m0 = 1, gamma = 5e-4, nu = 0.01, the adaptive CG
+    rule and the CP stop rule of Sec. 5.  The device run stops within a few
+    iterations of the exact-solve oracle and lands on the same density."""
+    import torch
+    N, nt = 16, 32
+    p = mi._problem(2, N, N, ("periodic", "periodic"), nt, 0.01, f_a=0.0, f_b=0.5, gamma=5e-4,
+                    max_cp=1000, cg_rule=1)
+    X, Y = mi.nodes(p)
+    V = -0.5 * (np.sin(2 * np.pi * Y) + np.sin(2 * np.pi * X) + np.cos(4 * np.pi * X))
+    m0 = np.ones((N, N))
+    p["cp_tol"] = 1e-4 * np.linalg.norm(m0)
+    W = np.zeros_like(V)
+    y0 = mi.initial_iterate(p, m0)
+    L = lib()
+    plan = L.mfg_plan(p, precision="mixed")
+    y = dev(y0)
+    ybar = y.clone()
+    z = torch.zeros(ops.sizes(p)[1], dtype=torch.float64, device="cuda")
+    rc, st = L.mfg_solve(plan, dev(m0), dev(V), dev(W), y, ybar, z)
+    assert rc == 0 and st[0].status == 0
+    ref = Solver(p, m0, V, W, method="modal").run(y0)
+    assert abs(st[0].cp_iters - ref["iters"]) <= max(3, 0.05 * ref["iters"])
+    assert st[0].r_last <= p["cp_tol"]
+    n = ops.sizes(p)[1]
+    assert rel(host(y)[:n], ref["y"][0]) <= 1e-3

@@ -75,3 +75,18 @@ def test_pcg_iterations_bounded(l, cap):
     x, it = solvers.pcg(lambda v: A @ v, lambda r: solvers.precond_modal(p, r), b, 1e-10)
     assert it <= cap
     assert np.linalg.norm(A @ x - b) <= 1e-10 * np.linalg.norm(b) * 1.0001
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("dim", [1, 2])
+def test_modal_applies_match_sparse(bc, dim):
+    """The matrix-free applies of AAt and P through the spatial eigenbasis equal
+    the assembled sparse matrices."""
+    p = mi.small(17, dim=dim, bc=bc, nx=9, ny=7, nt=6)["problem"]
+    v = mi.random_field(ops.sizes(p)[1], 5)
+    A = ops.AAt(p)
+    P = ops.precond(p)
+    assert np.linalg.norm(solvers.apply_AAt_modal(p, v) - A @ v) <= 1e-12 * np.linalg.norm(A @ v)
+    Pv, lam = solvers.apply_P_modal(p, v)
+    assert np.linalg.norm(Pv - P @ v) <= 1e-12 * np.linalg.norm(P @ v)
+    assert lam >= np.abs(np.linalg.eigvalsh(P.toarray())).max() * (1 - 1e-12)
