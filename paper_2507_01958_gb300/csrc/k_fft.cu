@@ -47,12 +47,25 @@ struct DotFuse {
   int flex;
 };
 
+// The PCG update fused into the first pass: z += alpha p, r -= alpha q for the
+// elements this block transforms, ||r||^2 accumulated, and the last block runs
+// the convergence test of k_update_zr.  The pass then transforms the new r.
+struct ZrFuse {
+  double* z;
+  double* r;
+  const double* p;
+  const double* q;
+  double* partials;
+  DevScalars* sc;
+};
+
 // tw[m] = (cos 2 pi m/N, sin 2 pi m/N), m < N/2;  dct[k] = (cos pi k/(2N), sin pi k/(2N)).
-template <typename T, int N, int MODE, bool CONTIG, typename TI, typename TO, bool DOT = false>
+template <typename T, int N, int MODE, bool CONTIG, typename TI, typename TO, bool DOT = false,
+          bool ZR = false>
 __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __restrict__ out,
                                              const T* __restrict__ tw, const T* __restrict__ dct,
                                              long long inner, long long nlines, const DevScalars* sc,
-                                             DotFuse df) {
+                                             DotFuse df, ZrFuse zf) {
   if (sc != nullptr && sc->cg_done) return;
   using Sh = FftShape<T, N>;
   constexpr int CL = Sh::CL, LB = Sh::LB, NP = Sh::NP;
@@ -69,7 +82,10 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
   const long long line0 = (long long)blockIdx.x * LB;
   const long long o = blockIdx.y;
 
-  // ---- load LB real lines
+  // ---- load LB real lines (with the fused z, r update when ZR)
+  double rr = 0.0;
+  double alpha = 0.0;
+  if constexpr (ZR) alpha = zf.sc->alpha;
   for (int idx = tid; idx < LB * N; idx += 256) {
     int l, i;
     if (CONTIG) { l = idx / N; i = idx % N; } else { i = idx / LB; l = idx % LB; }
@@ -77,7 +93,15 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
     T v = T(0);
     if (line < nlines) {
       const long long addr = CONTIG ? line * N + i : (o * N + i) * inner + line;
-      v = (T)in[addr];
+      if constexpr (ZR) {
+        zf.z[addr] = fma(alpha, zf.p[addr], zf.z[addr]);
+        const double rv = fma(-alpha, zf.q[addr], zf.r[addr]);
+        zf.r[addr] = rv;
+        rr = fma(rv, rv, rr);
+        v = (T)rv;
+      } else {
+        v = (T)in[addr];
+      }
     }
     if (MODE == FFT_DCT3) {
       real1[l * NP + i] = v;
@@ -177,6 +201,29 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
       }
     }
   }
+  if constexpr (ZR) {
+    double part[1] = {rr};
+    block_sum<1>(part);
+    if (!publish_and_check_last<1>(part, zf.partials, &zf.sc->counter)) return;
+    double tot[1];
+    gather_partials<1>(zf.partials, tot);
+    if (flat_tid() == 0) {
+      DevScalars* s = zf.sc;
+      s->rr = tot[0];
+      s->cg_it += 1;
+      const double tol = s->cg_tol;
+      if (!isfinite(tot[0])) {
+        s->cg_done = 1;
+        if (s->status == MFG_OK) s->status = MFG_ERR_NONFINITE;
+      } else if (tot[0] <= tol * tol * s->bnorm2) {
+        s->cg_done = 1;
+      } else if (s->cg_it >= s->max_cg) {
+        s->cg_done = 1;
+        if (s->status == MFG_OK) s->status = MFG_ERR_NOT_CONVERGED;
+      }
+      s->counter = 0;
+    }
+  }
   if constexpr (DOT) {
     double part[2] = {a0, a1};
     block_sum<2>(part);
@@ -208,20 +255,23 @@ long long fft_dot_partials(const Geom& g) {
   return 2 * ((nlines + lb - 1) / lb);
 }
 
-template <typename T, int N, int MODE, bool CONTIG, typename TI, typename TO, bool DOT = false>
+template <typename T, int N, int MODE, bool CONTIG, typename TI, typename TO, bool DOT = false,
+          bool ZR = false>
 static void launch_one(const TI* in, TO* out, const T* tw, const T* dct, long long inner,
                        long long outer, long long nlines, const DevScalars* sc, cudaStream_t s,
-                       DotFuse df = DotFuse{}) {
+                       DotFuse df = DotFuse{}, ZrFuse zf = ZrFuse{}) {
   using Sh = FftShape<T, N>;
   dim3 grid((unsigned)((nlines + Sh::LB - 1) / Sh::LB), CONTIG ? 1u : (unsigned)outer);
-  k_fft<T, N, MODE, CONTIG, TI, TO, DOT><<<grid, 256, Sh::smem, s>>>(in, out, tw, dct, inner, nlines, sc, df);
+  k_fft<T, N, MODE, CONTIG, TI, TO, DOT, ZR><<<grid, 256, Sh::smem, s>>>(in, out, tw, dct, inner, nlines, sc,
+                                                                         df, zf);
 }
 
-template <typename T, int MODE, bool CONTIG, typename TI, typename TO, bool DOT = false>
+template <typename T, int MODE, bool CONTIG, typename TI, typename TO, bool DOT = false,
+          bool ZR = false>
 static int set_attr_one() {
   int bad = 0;
 #define MFG_FFT_ATTR(NN)                                                                      \
-  bad |= cudaFuncSetAttribute(k_fft<T, NN, MODE, CONTIG, TI, TO, DOT>,                       \
+  bad |= cudaFuncSetAttribute(k_fft<T, NN, MODE, CONTIG, TI, TO, DOT, ZR>,                   \
                               cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
                               (int)FftShape<T, NN>::smem) != cudaSuccess;
   MFG_FFT_ATTR(8) MFG_FFT_ATTR(16) MFG_FFT_ATTR(32) MFG_FFT_ATTR(64) MFG_FFT_ATTR(128)
@@ -230,23 +280,37 @@ static int set_attr_one() {
   return bad;
 }
 
-template <typename T, int MODE, bool CONTIG, typename TI, typename TO, bool DOT = false>
+template <typename T, int MODE, bool CONTIG, typename TI, typename TO, bool DOT = false,
+          bool ZR = false>
 static void dispatch(int N, const TI* in, TO* out, const T* tw, const T* dct, long long inner,
                      long long outer, long long nlines, const DevScalars* sc, cudaStream_t s,
-                     DotFuse df = DotFuse{}) {
+                     DotFuse df = DotFuse{}, ZrFuse zf = ZrFuse{}) {
   switch (N) {
-#define MFG_FFT_CASE(NN) \
-    case NN: launch_one<T, NN, MODE, CONTIG, TI, TO, DOT>(in, out, tw, dct, inner, outer, nlines, sc, s, df); break;
+#define MFG_FFT_CASE(NN)                                                                              \
+    case NN:                                                                                          \
+      launch_one<T, NN, MODE, CONTIG, TI, TO, DOT, ZR>(in, out, tw, dct, inner, outer, nlines, sc, s, df, zf); \
+      break;
     MFG_FFT_CASE(8) MFG_FFT_CASE(16) MFG_FFT_CASE(32) MFG_FFT_CASE(64) MFG_FFT_CASE(128) MFG_FFT_CASE(256)
 #undef MFG_FFT_CASE
-    default: launch_one<T, 512, MODE, CONTIG, TI, TO, DOT>(in, out, tw, dct, inner, outer, nlines, sc, s, df); break;
+    default:
+      launch_one<T, 512, MODE, CONTIG, TI, TO, DOT, ZR>(in, out, tw, dct, inner, outer, nlines, sc, s, df, zf);
+      break;
   }
 }
 
-// y axis (contiguous), first pass: FP64 residual in, T out.
+// y axis (contiguous), first pass: FP64 residual in, T out; with zr != nullptr
+// the PCG update z += alpha p, r -= alpha q and its convergence test come first.
 template <typename T>
 void fft_y_forward(int N, int periodic, const double* in, T* out, const T* tw, const T* dct,
-                   long long nlines, const DevScalars* sc, cudaStream_t s) {
+                   long long nlines, const DevScalars* sc, cudaStream_t s, const PcgZr* zr) {
+  if (zr) {
+    ZrFuse zf{zr->z, zr->r, zr->p, zr->q, zr->partials, zr->sc};
+    if (periodic)
+      dispatch<T, FFT_DHT, true, double, T, false, true>(N, in, out, tw, dct, 1, 1, nlines, sc, s, DotFuse{}, zf);
+    else
+      dispatch<T, FFT_DCT2, true, double, T, false, true>(N, in, out, tw, dct, 1, 1, nlines, sc, s, DotFuse{}, zf);
+    return;
+  }
   if (periodic)
     dispatch<T, FFT_DHT, true, double, T>(N, in, out, tw, dct, 1, 1, nlines, sc, s);
   else
@@ -283,9 +347,9 @@ void fft_x(int N, int periodic, int inverse, const T* in, T* out, const T* tw, c
 }
 
 template void fft_y_forward<float>(int, int, const double*, float*, const float*, const float*, long long,
-                                   const DevScalars*, cudaStream_t);
+                                   const DevScalars*, cudaStream_t, const PcgZr*);
 template void fft_y_forward<double>(int, int, const double*, double*, const double*, const double*, long long,
-                                    const DevScalars*, cudaStream_t);
+                                    const DevScalars*, cudaStream_t, const PcgZr*);
 template void fft_y_inverse<float>(int, int, const float*, double*, const float*, const float*, long long,
                                    const DevScalars*, cudaStream_t, const PcgDot*);
 template void fft_y_inverse<double>(int, int, const double*, double*, const double*, const double*, long long,
@@ -305,6 +369,10 @@ int fft_configure() {
   bad |= set_attr_one<float, FFT_DCT3, true, float, double, true>();
   bad |= set_attr_one<double, FFT_DHT, true, double, double, true>();
   bad |= set_attr_one<double, FFT_DCT3, true, double, double, true>();
+  bad |= set_attr_one<float, FFT_DHT, true, double, float, false, true>();
+  bad |= set_attr_one<float, FFT_DCT2, true, double, float, false, true>();
+  bad |= set_attr_one<double, FFT_DHT, true, double, double, false, true>();
+  bad |= set_attr_one<double, FFT_DCT2, true, double, double, false, true>();
   bad |= set_attr_one<float, FFT_DHT, false, float, float>();
   bad |= set_attr_one<float, FFT_DCT2, false, float, float>();
   bad |= set_attr_one<float, FFT_DCT3, false, float, float>();

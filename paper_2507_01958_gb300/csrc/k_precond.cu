@@ -503,15 +503,18 @@ template <typename T>
 static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, const T* lamt,
                           const T* L1, const T* L2, const T* twx, const T* dctx, const T* twy,
                           const T* dcty, const double* r, double* z, T* w0, T* w1,
-                          const DevScalars* sc, cudaStream_t s, const PcgDot* dot) {
+                          const DevScalars* sc, cudaStream_t s, const PcgDot* dot,
+                          const PcgZr* zr) {
   const long long S = g.S, n = g.n;
   const bool fy = twy != nullptr && fft_supported(g.ny);
   const bool fx = twx != nullptr && fft_supported(g.nx);
   // y forward: axis length ny, contiguous
-  if (fy)
-    fft_y_forward<T>(g.ny, g.pery, r, w0, twy, dcty, n / g.ny, sc, s);
-  else
+  if (fy) {
+    fft_y_forward<T>(g.ny, g.pery, r, w0, twy, dcty, n / g.ny, sc, s, zr);
+  } else {
+    if (zr) launch_update_zr(n, zr->z, zr->r, zr->p, zr->q, zr->partials, zr->sc, s);
     axis_pass<double, T, T>(r, w0, Hy, g.ny, 1, n / g.ny, 0, sc, s);
+  }
   T* a = w0;
   T* b = w1;
   if (g.nx > 1) {
@@ -540,21 +543,21 @@ static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, c
 
 void launch_precond(const Geom& g, const PrecTables& t, int precision, const double* r, double* z,
                     double* work64, float* work32, const DevScalars* sc, cudaStream_t s,
-                    const PcgDot* dot) {
+                    const PcgDot* dot, const PcgZr* zr) {
   if (precision == MFG_MIXED)
     precond_typed<float>(g, t.Hx32, t.Hy32, t.Vt32, t.lamt32, t.L1_32, t.L2_32, t.twx32, t.dctx32,
-                         t.twy32, t.dcty32, r, z, work32, work32 + g.n, sc, s, dot);
+                         t.twy32, t.dcty32, r, z, work32, work32 + g.n, sc, s, dot, zr);
   else
     precond_typed<double>(g, t.Hx64, t.Hy64, t.Vt64, t.lamt64, t.L1_64, t.L2_64, t.twx64, t.dctx64,
-                          t.twy64, t.dcty64, r, z, work64, work64 + g.n, sc, s, dot);
+                          t.twy64, t.dcty64, r, z, work64, work64 + g.n, sc, s, dot, zr);
 }
 
 int precond_kernel_count(const Geom& g) { return g.nx > 1 ? 5 : 3; }
 
-// Kernels of a preconditioner apply that also forms the PCG dot products.
-int precond_dot_kernel_count(const Geom& g, const PrecTables& t) {
+// Kernels of a preconditioner apply that also runs the PCG update and dot products.
+int precond_step_kernel_count(const Geom& g, const PrecTables& t) {
   const bool fused = t.twy32 != nullptr && fft_supported(g.ny);
-  return precond_kernel_count(g) + (fused ? 0 : 1);
+  return precond_kernel_count(g) + (fused ? 0 : 2);
 }
 
 // Opt-in shared memory for the time pass; called once per device before any

@@ -175,7 +175,7 @@ int check_b(mfg_plan_t pl, int b) {
 
 // kernels per CP iteration outside PCG (rhs, precond, init_p, arm, prox) and per PCG iteration
 int launches_cp(const Inst& in) { return 4 + precond_kernel_count(in.g); }
-int launches_cg(const Inst& in) { return 3 + precond_dot_kernel_count(in.g, in.tabs); }
+int launches_cg(const Inst& in) { return 2 + precond_step_kernel_count(in.g, in.tabs); }
 
 // Captures the per-instance CP loop into `top` as a while-node branch.
 int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, const double* V,
@@ -219,9 +219,9 @@ int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, con
   cudaStream_t s2 = pl->cap1;
   CK(cudaStreamBeginCaptureToGraph(s2, body_cg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   const PcgDot dot{in.r, in.q, in.partials, in.sc, flex};
+  const PcgZr zr{z, in.r, in.pv, in.q, in.partials, in.sc};
   launch_AAt(g, in.pv, in.q, in.partials, in.sc, 1, s2);
-  launch_update_zr(g.n, z, in.r, in.pv, in.q, in.partials, in.sc, s2);
-  launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s2, &dot);
+  launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s2, &dot, &zr);
   launch_update_p(g.n, in.zp, in.pv, in.sc, hg, 1, s2);
   CK(cudaStreamEndCapture(s2, &body_cg));
   return MFG_OK;
@@ -274,11 +274,11 @@ int solve_eager(mfg_plan_t pl, const double* m0, const double* V, const double* 
         CK(cudaStreamSynchronize(s));
         if (hs.cg_done) break;
         const PcgDot dot{in.r, in.q, in.partials, in.sc, flex};
+        const PcgZr zr{zb, in.r, in.pv, in.q, in.partials, in.sc};
         launch_AAt(g, in.pv, in.q, in.partials, in.sc, 1, s);
-        launch_update_zr(g.n, zb, in.r, in.pv, in.q, in.partials, in.sc, s);
-        launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s, &dot);
+        launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s, &dot, &zr);
         launch_update_p(g.n, in.zp, in.pv, in.sc, 0, 0, s);
-        pl->launches += 3 + precond_dot_kernel_count(g, in.tabs);
+        pl->launches += 2 + precond_step_kernel_count(g, in.tabs);
       }
       launch_prox_cp(g, in.cf, zb, yb, ybb, Vb, Wb, in.partials, in.sc, 0, 0, s);
       pl->launches += 1;
@@ -535,12 +535,12 @@ int mfg_adjoint(mfg_plan_t pl, int b, const double* y, const double* z, const do
     CK(cudaStreamSynchronize(s));
     if (hs.cg_done) break;
     const PcgDot dot{in.r, in.q, in.partials, in.sc, flex};
+    const PcgZr zr{in.adj_eta, in.r, in.pv, in.q, in.partials, in.sc};
     launch_ct_hinv(g, in.cf, y, in.pv, nullptr, in.adj_t, s, in.sc);
     launch_apply_C(g, in.adj_t, in.q, 1.0, nullptr, in.partials, in.sc, 2, s, in.pv);
-    launch_update_zr(g.n, in.adj_eta, in.r, in.pv, in.q, in.partials, in.sc, s);
-    launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s, &dot);
+    launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s, &dot, &zr);
     launch_update_p(g.n, in.zp, in.pv, in.sc, 0, 0, s);
-    launches += 4 + precond_dot_kernel_count(g, in.tabs);
+    launches += 3 + precond_step_kernel_count(g, in.tabs);
   }
   // mu = H^{-1}(g - C^T eta), then the contractions
   launch_ct_hinv(g, in.cf, y, in.adj_eta, gy, in.adj_t, s, nullptr);

@@ -111,14 +111,26 @@ struct PcgDot {
   DevScalars* sc;
   int flex;
 };
+// The PCG step z += alpha p, r -= alpha q (with its convergence test) that the
+// first preconditioner pass can fuse.
+struct PcgZr {
+  double* z;
+  double* r;
+  const double* p;
+  const double* q;
+  double* partials;
+  DevScalars* sc;
+};
 // z = P^{-1} r.  work64: 2n doubles (FP64 path); work32: 2n floats (mixed path).
-// With dot != nullptr the PCG dot products and beta are formed as well (fused
-// into the last pass when it is an FFT pass, else by k_dot_beta).
+// With zr != nullptr the PCG update of (z, r) runs first (fused into the first
+// pass when it is an FFT pass, else by k_update_zr), and the transform is of
+// the updated r; with dot != nullptr the PCG dot products and beta are formed
+// afterwards (fused into the last FFT pass, else by k_dot_beta).
 void launch_precond(const Geom& g, const PrecTables& t, int precision, const double* r, double* z,
                     double* work64, float* work32, const DevScalars* sc, cudaStream_t s,
-                    const PcgDot* dot = nullptr);
+                    const PcgDot* dot = nullptr, const PcgZr* zr = nullptr);
 int precond_kernel_count(const Geom& g);
-int precond_dot_kernel_count(const Geom& g, const PrecTables& t);
+int precond_step_kernel_count(const Geom& g, const PrecTables& t);
 int precond_configure();
 
 // FFT spatial passes (k_fft.cu).
@@ -127,7 +139,7 @@ long long fft_dot_partials(const Geom& g);
 int fft_configure();
 template <typename T>
 void fft_y_forward(int N, int periodic, const double* in, T* out, const T* tw, const T* dct,
-                   long long nlines, const DevScalars* sc, cudaStream_t s);
+                   long long nlines, const DevScalars* sc, cudaStream_t s, const PcgZr* zr);
 template <typename T>
 void fft_y_inverse(int N, int periodic, const T* in, double* out, const T* tw, const T* dct,
                    long long nlines, const DevScalars* sc, cudaStream_t s, const PcgDot* dot);
