@@ -185,6 +185,36 @@ def adjoint_measure(dev, cp_iters=300):
             "final_rel_residual": st.r_last, "status": int(rc), "dnu": float(dnu.item())}
 
 
+def exact_time_measure(dev, L, insts, m0, V, W, y0, stream, cp_iters=CP_PER_STEP):
+    """The same four-instance step with l = 0 (time blocks solved exactly per
+    spatial mode, P = AAt; not the paper's preconditioner): CP iterations/s and
+    PCG iterations per CP iteration, mixed precision."""
+    import torch
+    probs = [dict(i["problem"], max_cp=cp_iters, cg_tol=CG_TOL, precision="mixed", l=0) for i in insts]
+    plan = L.mfg_plan(probs)
+    y, ybar = torch.empty_like(y0), torch.empty_like(y0)
+    z = torch.zeros(L.mfg_sizes(plan)["dual"], dtype=torch.float64, device=dev)
+
+    def step():
+        y.copy_(y0)
+        ybar.copy_(y0)
+        z.zero_()
+        return L.mfg_solve(plan, m0, V, W, y, ybar, z, stream=stream)[1]
+
+    step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    st = step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    cp = sum(s.cp_iters for s in st)
+    cg = sum(s.cg_iters for s in st)
+    return {"workload": "same 4-instance step, l = 0 (exact time solve, P = AAt)", "value": cp / t,
+            "unit": "CP iterations/s", "avg_pcg_per_cp": cg / max(cp, 1), "ms_per_step": 1e3 * t}
+
+
 def batch_measure(dev, count=64, cp_iters=20):  # noqa: C901
     """The uneven batch: `count` seeded instances (periodic or Neumann, N in
     {64,128,256}, N_t in {32,64,128}, nu log-uniform) in one plan and one graph
@@ -371,6 +401,7 @@ def run_gpu(args):
     h2d = 8 * (3 * sz["field"] + 2 * sz["primal"] + sz["dual"])
     d2h = 8 * (2 * sz["primal"] + sz["dual"])
 
+    exact = exact_time_measure(dev, L, insts, m0, V, W, y0, stream) if not args.no_extras else None
     adj = adjoint_measure(dev) if not args.no_extras else None
     batch = batch_measure(dev) if not args.no_extras else None
 
@@ -414,6 +445,7 @@ def run_gpu(args):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk,
+            "exact_time_solve": exact,
             "adjoint": adj,
             "batch_uneven": batch,
         }
@@ -516,7 +548,7 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cp-per-step", type=int, default=CP_PER_STEP)
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_df", "fp64"])
     ap.add_argument("--quick", action="store_true", help="main timed loop only (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and uneven-batch lines")
     ap.add_argument("--kernels-only", action="store_true",

@@ -54,8 +54,11 @@ enum mfg_status {
 enum { MFG_PERIODIC = 0, MFG_NEUMANN = 1 };
 /* MFG_FP64: every step in FP64.  MFG_MIXED: the preconditioner (transforms and
  * per-frequency division) in FP32 inside FP64 flexible PCG; AAt, residuals,
- * dot products and the prox stay FP64. */
-enum { MFG_FP64 = 0, MFG_MIXED = 1 };
+ * dot products and the prox stay FP64.  MFG_MIXED_DF: as MFG_MIXED, with the
+ * AAt stencil evaluated in double-float arithmetic (pairs of FP32 numbers,
+ * ~48 significant bits) from FP64 inputs to FP64 outputs; residuals, dot
+ * products and the prox stay FP64.  GB300 issues FP32 at ~58x its FP64 rate. */
+enum { MFG_FP64 = 0, MFG_MIXED = 1, MFG_MIXED_DF = 2 };
 /* PCG tolerance: fixed cg_tol, or the paper's rule
  * min{1e-4, max{1e-6, 1e-4 r}} with r the last CP step (Sec. 5). */
 enum { MFG_CG_FIXED = 0, MFG_CG_ADAPTIVE = 1 };
@@ -72,7 +75,10 @@ typedef struct {
   double qprime;     /* Hamiltonian exponent q' of eq. power_hamiltonian; only 2      */
   double f_a, f_b;   /* f(x,m) = f_a m + f_b m^2 + V(x); f_a, f_b >= 0 (monotone f)   */
   double g_a;        /* g(x,m) = g_a m + W(x); g_a >= 0                                */
-  int l;             /* time preconditioner: 1 = DCT-VIII, 2 = DST-I (Sec. 4.1)       */
+  int l;             /* time preconditioner: 1 = DCT-VIII, 2 = DST-I (Sec. 4.1);
+                        0 = no approximation in the first block (P = AAt): the time
+                        blocks are solved exactly per spatial mode by tridiagonal
+                        elimination (not in the paper; see mfg_apply_precond)      */
   double gamma;      /* acceleration constant gamma > 0 (Sec. 5)                       */
   double tau0, sigma0; /* initial step sizes (Sec. 5: 1 and 1)                         */
   int max_cp;        /* CP iterations per mfg_solve call                               */
@@ -80,7 +86,7 @@ typedef struct {
   int cg_rule;       /* MFG_CG_FIXED | MFG_CG_ADAPTIVE                                 */
   double cg_tol;     /* relative PCG tolerance for MFG_CG_FIXED                        */
   int max_cg;        /* PCG iteration cap per solve                                    */
-  int precision;     /* MFG_FP64 | MFG_MIXED                                           */
+  int precision;     /* MFG_FP64 | MFG_MIXED | MFG_MIXED_DF                            */
 } mfg_problem;
 
 /* Per-instance run record.  On entry to mfg_solve, `ell`, `tau`, `sigma` are
@@ -102,7 +108,7 @@ typedef struct mfg_plan_s* mfg_plan_t;
  * lines 1-10) and transform matrices on the host in FP64, uploads them and
  * allocates all device workspace on the current device.  Rejects q' != 2
  * (MFG_ERR_UNSUPPORTED), N_t < 2, N < 2, T <= 0, nu < 0, f_a/f_b/g_a < 0,
- * l not in {1,2}, N_t > 256 (UNSUPPORTED).  *out is NULL on failure. */
+ * l not in {0,1,2}, N_t > 256 (UNSUPPORTED).  *out is NULL on failure. */
 int mfg_plan(const mfg_problem* probs, int batch, mfg_plan_t* out);
 
 /* Frees all plan-owned memory.  NULL is accepted. */
@@ -142,7 +148,10 @@ int mfg_solve_host(mfg_plan_t plan, const double* m0, const double* V,
                    mfg_stats* st, void* stream);
 
 /* z = P^{-1} r for instance b (Alg. 1 with Alg. 2 in place of line 6, eq.
- * pstrec), in the plan's precision.  r, z: n elements; must not alias. */
+ * pstrec), in the plan's precision.  With l = 0 the time transform and the
+ * per-frequency division are replaced by an exact tridiagonal solve in time per
+ * spatial mode, so P = AAt (eq. largeA) up to rounding.  r, z: n elements;
+ * must not alias. */
 int mfg_apply_precond(mfg_plan_t plan, int b, const double* r, double* z, void* stream);
 
 /* y = prox_{tau phi}(v) for instance b, cell by cell (Sec. 3; phi_ij = b_hat +

@@ -105,7 +105,7 @@ int build_prec_tables(const mfg_problem& p, const Geom& g, PrecTables* t, std::s
   std::vector<double> Hx, lx, Hy, ly, V, lt;
   axis_basis(g.nx, g.perx, Hx, lx);
   axis_basis(g.ny, g.pery, Hy, ly);
-  time_basis(g.nt, p.l, V, lt);
+  time_basis(g.nt, p.l == 0 ? 2 : p.l, V, lt);  // l = 0 has no time transform (unused table)
   const double dx_defect = std::fmax(ortho_defect(Hx, g.nx), ortho_defect(Hy, g.ny));
   const double dt_defect = ortho_defect(V, g.nt);
   if (dx_defect > 1e-10 || dt_defect > 1e-10) {
@@ -120,6 +120,43 @@ int build_prec_tables(const mfg_problem& p, const Geom& g, PrecTables* t, std::s
     return MFG_ERR_INVALID_ARG;
   }
   std::vector<double> L1((size_t)g.S), L2((size_t)g.S);
+  if (p.l == 0) {
+    // Exact variant (P = AAt): per spatial mode with Laplacian eigenvalue kappa,
+    // the block of eq. largeA is the SPD tridiagonal matrix with diagonal
+    // (C, C + 1/dt^2, ...), C = L^2 + 2 kappa, L = nu kappa + 1/dt, and
+    // off-diagonal -L/dt.  Its Thomas factors depend only on the mode, so they
+    // are formed once here: c_k = off/den_k and 1/den_k, den_k = diag_k - off c_{k-1}.
+    std::vector<double> cf((size_t)g.n), idn((size_t)g.n), off((size_t)g.S);
+    const double dtv = 1.0 / g.idt;
+    for (int a = 0; a < g.nx; ++a)
+      for (int b = 0; b < g.ny; ++b) {
+        const size_t sidx = (size_t)a * g.ny + b;
+        const double kap = lx[a] * g.ax + ly[b] * g.ay;
+        const double Ls = g.nu * kap + 1.0 / dtv;
+        const double Cs = Ls * Ls + 2.0 * kap;
+        const double o = -Ls / dtv;
+        off[sidx] = o;
+        double cprev = 0.0;
+        for (int k = 0; k < g.nt; ++k) {
+          const double diag = Cs + (k >= 1 ? 1.0 / (dtv * dtv) : 0.0);
+          const double den = diag - (k >= 1 ? o * cprev : 0.0);
+          const size_t e = (size_t)k * g.S + sidx;
+          idn[e] = 1.0 / den;
+          cprev = o / den;
+          cf[e] = cprev;
+        }
+      }
+    t->thc64 = upload<double>(cf, err);
+    t->thd64 = upload<double>(idn, err);
+    t->tho64 = upload<double>(off, err);
+    t->thc32 = upload<float>(cf, err);
+    t->thd32 = upload<float>(idn, err);
+    t->tho32 = upload<float>(off, err);
+    if (!t->thc64 || !t->thd64 || !t->tho64 || !t->thc32 || !t->thd32 || !t->tho32) {
+      free_prec_tables(t);
+      return MFG_ERR_CUDA;
+    }
+  }
   const double dtv = 1.0 / g.idt, nu = g.nu;
   for (int a = 0; a < g.nx; ++a)
     for (int b = 0; b < g.ny; ++b) {
@@ -171,7 +208,8 @@ int build_prec_tables(const mfg_problem& p, const Geom& g, PrecTables* t, std::s
 void free_prec_tables(PrecTables* t) {
   void* ptrs[] = {t->Hx64, t->Hy64, t->Vt64, t->lamt64, t->L1_64, t->L2_64, t->Hx32, t->Hy32,
                   t->Vt32, t->lamt32, t->L1_32, t->L2_32, t->twx64, t->twx32, t->dctx64, t->dctx32,
-                  t->twy64, t->twy32, t->dcty64, t->dcty32};
+                  t->twy64, t->twy32, t->dcty64, t->dcty32, t->thc64, t->thd64, t->tho64,
+                  t->thc32, t->thd32, t->tho32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   *t = PrecTables{};
@@ -486,6 +524,35 @@ static void launch_time_fast(const T* in, T* out, const T* V, const T* lamt, con
   k_time_fast<T, NT><<<blocks, 256, Sh::smem, s>>>(in, out, V, lamt, L1, L2, S, sc);
 }
 
+// Exact time solve of the l = 0 variant: per spatial mode s, the tridiagonal
+// system of eq. largeA in time by Thomas elimination with the precomputed
+// factors (forward sweep into `out`, then back substitution in place).  One
+// thread per mode; loads at a fixed k are contiguous across the threads.
+template <typename T>
+__global__ void __launch_bounds__(256) k_thomas(const T* __restrict__ in, T* __restrict__ out,
+                                                const T* __restrict__ cf, const T* __restrict__ idn,
+                                                const T* __restrict__ off, int nt, int S,
+                                                const DevScalars* sc) {
+  if (sc != nullptr && sc->cg_done) return;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
+    const T o = off[s];
+    T d = T(0);
+#pragma unroll 8
+    for (int k = 0; k < nt; ++k) {
+      const long long e = (long long)k * S + s;
+      d = (in[e] - o * d) * idn[e];
+      out[e] = d;
+    }
+    T x = d;
+#pragma unroll 8
+    for (int k = nt - 2; k >= 0; --k) {
+      const long long e = (long long)k * S + s;
+      x = out[e] - cf[e] * x;
+      out[e] = x;
+    }
+  }
+}
+
 template <typename T>
 static size_t time_smem(int nt) { return sizeof(T) * (size_t)nt * (TSW + TCH); }
 
@@ -502,7 +569,8 @@ static void time_pass(const T* in, T* out, const T* V, const T* lamt, const T* L
 template <typename T>
 static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, const T* lamt,
                           const T* L1, const T* L2, const T* twx, const T* dctx, const T* twy,
-                          const T* dcty, const double* r, double* z, T* w0, T* w1,
+                          const T* dcty, const T* thc, const T* thd, const T* tho,
+                          const double* r, double* z, T* w0, T* w1,
                           const DevScalars* sc, cudaStream_t s, const PcgDot* dot,
                           const PcgZr* zr) {
   const long long S = g.S, n = g.n;
@@ -524,7 +592,10 @@ static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, c
       axis_pass<T, T, T>(a, b, Hx, g.nx, g.ny, (long long)g.nt, 0, sc, s);
     T* t = a; a = b; b = t;
   }
-  time_pass<T>(a, b, V, lamt, L1, L2, g.nt, (int)S, sc, s);
+  if (thc != nullptr)
+    k_thomas<T><<<(int)((S + 255) / 256), 256, 0, s>>>(a, b, thc, thd, tho, g.nt, (int)S, sc);
+  else
+    time_pass<T>(a, b, V, lamt, L1, L2, g.nt, (int)S, sc, s);
   { T* t = a; a = b; b = t; }
   if (g.nx > 1) {
     if (fx)
@@ -544,12 +615,14 @@ static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, c
 void launch_precond(const Geom& g, const PrecTables& t, int precision, const double* r, double* z,
                     double* work64, float* work32, const DevScalars* sc, cudaStream_t s,
                     const PcgDot* dot, const PcgZr* zr) {
-  if (precision == MFG_MIXED)
+  if (precision == MFG_MIXED || precision == MFG_MIXED_DF)
     precond_typed<float>(g, t.Hx32, t.Hy32, t.Vt32, t.lamt32, t.L1_32, t.L2_32, t.twx32, t.dctx32,
-                         t.twy32, t.dcty32, r, z, work32, work32 + g.n, sc, s, dot, zr);
+                         t.twy32, t.dcty32, t.thc32, t.thd32, t.tho32, r, z, work32, work32 + g.n,
+                         sc, s, dot, zr);
   else
     precond_typed<double>(g, t.Hx64, t.Hy64, t.Vt64, t.lamt64, t.L1_64, t.L2_64, t.twx64, t.dctx64,
-                          t.twy64, t.dcty64, r, z, work64, work64 + g.n, sc, s, dot, zr);
+                          t.twy64, t.dcty64, t.thc64, t.thd64, t.tho64, r, z, work64, work64 + g.n,
+                          sc, s, dot, zr);
 }
 
 int precond_kernel_count(const Geom& g) { return g.nx > 1 ? 5 : 3; }

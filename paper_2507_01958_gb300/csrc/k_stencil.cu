@@ -10,6 +10,7 @@
 // entries past the ends; on a periodic axis indices wrap.  Both cases use one
 // rule: a point has a "minus" neighbour (hm) and a "plus" neighbour (hp) unless
 // it sits at the matching end of a Neumann axis.
+#include "df64.cuh"
 #include "mfg_internal.cuh"
 #include "reduce.cuh"
 
@@ -348,11 +349,139 @@ __global__ void __launch_bounds__(TI * TJ, 2) k_AAt(Geom g, int kc, const double
   }
 }
 
+// The same fused stencil in double-float arithmetic (df64.cuh): p is split into
+// FP32 pairs as it is staged, every stencil operation runs on FP32 pairs, and q
+// is rebuilt in FP64 (one FP64 add per point) together with the FP64 p.q.
+// About 48 significant bits; used by the MFG_MIXED_DF precision.
+__device__ __forceinline__ void load_plane_h2_df(const Geom& g, const double* __restrict__ p, int k,
+                                                 int i0, int j0, df (*dst)[H2J]) {
+  const int tid = threadIdx.x + TJ * threadIdx.y;
+  if (k >= g.nt) {
+    for (int s = tid; s < H2I * H2J; s += TI * TJ) dst[s / H2J][s % H2J] = df{0.0f, 0.0f};
+    return;
+  }
+  const double* pk = p + (long long)k * g.S;
+  for (int s = tid; s < H2I * H2J; s += TI * TJ) {
+    const int li = s / H2J, lj = s % H2J;
+    const int gi = halo_index(i0 + li - 2, g.nx, g.perx);
+    const int gj = halo_index(j0 + lj - 2, g.ny, g.pery);
+    dst[li][lj] = df_from_double(pk[(long long)gi * g.ny + gj]);
+  }
+}
+
+template <int ACTX, int WID>
+__device__ __forceinline__ df fast_K_df(const df (*A)[WID], int r, int c, df ax, df ay, df cK) {
+  df t = df_mul(ay, df_add(A[r][c - 1], A[r][c + 1]));
+  if (ACTX) t = df_add(t, df_mul(ax, df_add(A[r - 1][c], A[r + 1][c])));
+  return df_sub(df_mul(cK, A[r][c]), t);
+}
+
+template <int ACTX>
+__global__ void __launch_bounds__(TI * TJ, 2) k_AAt_df(Geom g, int kc, const double* __restrict__ p,
+                                                       double* __restrict__ q, double* partials,
+                                                       DevScalars* sc, int mode) {
+  if (mode == 1 && sc->cg_done) return;
+  __shared__ df P[2][H2I][H2J];
+  __shared__ df XM[H1I][H1J];
+  __shared__ df KP[TI][TJ];
+  const int tj = threadIdx.x, ti = threadIdx.y;
+  const int j0 = blockIdx.x * TJ, i0 = blockIdx.y * TI;
+  const int k0 = blockIdx.z * kc;
+  const int k1 = min(g.nt, k0 + kc);
+  const int gi = i0 + ti, gj = j0 + tj;
+  const bool own = gi < g.nx && gj < g.ny;
+  const double axd = ACTX ? g.ax : 0.0, ayd = g.ay, cKd = 2.0 * (axd + ayd);
+  const df ax = df_from_double(axd), ay = df_from_double(ayd), cK = df_from_double(cKd);
+  const df nax = df_from_double(g.nu * axd), nay = df_from_double(g.nu * ayd),
+           ncK = df_from_double(g.nu * cKd);
+  const df nu = df_from_double(g.nu), idt = df_from_double(g.idt), two = df{2.0f, 0.0f};
+  const bool ghost_x = ACTX && !g.perx && (i0 == 0 || i0 + TI >= g.nx);
+  const bool ghost_y = !g.pery && (j0 == 0 || j0 + TJ >= g.ny);
+  const bool ghosts = ghost_x || ghost_y;
+  const int tid = tj + TJ * ti;
+
+  int cur = 0;
+  load_plane_h2_df(g, p, k0, i0, j0, P[cur]);
+  df xprev{0.0f, 0.0f};
+  if (k0 > 0) {
+    load_plane_h2_df(g, p, k0 - 1, i0, j0, P[cur ^ 1]);
+    __syncthreads();
+    if (own)
+      xprev = df_add(fast_K_df<ACTX, H2J>(P[cur ^ 1], ti + 2, tj + 2, nax, nay, ncK),
+                     df_mul(df_sub(P[cur ^ 1][ti + 2][tj + 2], P[cur][ti + 2][tj + 2]), idt));
+    __syncthreads();
+  }
+  double acc = 0.0;
+  for (int k = k0; k < k1; ++k) {
+    load_plane_h2_df(g, p, k + 1, i0, j0, P[cur ^ 1]);
+    __syncthreads();
+    const df (*Pk)[H2J] = P[cur];
+    const df (*Pn)[H2J] = P[cur ^ 1];
+    for (int s = tid; s < H1I * H1J; s += TI * TJ) {
+      const int li = s / H1J, lj = s % H1J;
+      const df kp = fast_K_df<ACTX, H2J>(Pk, li + 1, lj + 1, ax, ay, cK);
+      XM[li][lj] = df_add(df_mul(nu, kp), df_mul(df_sub(Pk[li + 1][lj + 1], Pn[li + 1][lj + 1]), idt));
+      if (li >= 1 && li <= TI && lj >= 1 && lj <= TJ) KP[li - 1][lj - 1] = kp;
+    }
+    __syncthreads();
+    if (ghosts) {
+      for (int s = tid; s < H1I * H1J; s += TI * TJ) {
+        const int li = s / H1J, lj = s % H1J;
+        const int xi = i0 + li - 1, xj = j0 + lj - 1;
+        const bool ox = ghost_x && (xi < 0 || xi >= g.nx);
+        const bool oy = ghost_y && (xj < 0 || xj >= g.ny);
+        if (ox || oy) {
+          const int mi = ox ? (xi < 0 ? li + 1 : li - 1) : li;
+          const int mj = oy ? (xj < 0 ? lj + 1 : lj - 1) : lj;
+          XM[li][lj] = XM[mi][mj];
+        }
+      }
+      __syncthreads();
+    }
+    if (own) {
+      const df c = XM[ti + 1][tj + 1];
+      const df nKxm = fast_K_df<ACTX, H1J>(XM, ti + 1, tj + 1, nax, nay, ncK);
+      const df val = df_add(df_mul(two, KP[ti][tj]), df_add(df_mul(df_sub(c, xprev), idt), nKxm));
+      xprev = c;
+      const long long e = (long long)k * g.S + (long long)gi * g.ny + gj;
+      const double vd = df_to_double(val);
+      q[e] = vd;
+      acc = fma(vd, p[e], acc);
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  if (mode != 1) return;
+  double part[1] = {acc};
+  block_sum<1>(part);
+  if (!publish_and_check_last<1>(part, partials, &sc->counter)) return;
+  double tot[1];
+  gather_partials<1>(partials, tot);
+  if (flat_tid() == 0) {
+    sc->pq = tot[0];
+    if (tot[0] > 0.0 && isfinite(tot[0])) {
+      sc->alpha = sc->rz / tot[0];
+    } else {
+      sc->alpha = 0.0;
+      sc->cg_done = 1;
+      if (sc->status == MFG_OK) sc->status = MFG_ERR_NONFINITE;
+    }
+    sc->counter = 0;
+  }
+}
+
 void launch_AAt(const Geom& g, const double* p, double* q, double* partials, DevScalars* sc,
-                int mode, cudaStream_t s) {
+                int mode, cudaStream_t s, int df64) {
   const int kc = aat_chunk(g);
   dim3 grid((g.ny + TJ - 1) / TJ, (g.nx + TI - 1) / TI, (g.nt + kc - 1) / kc);
   dim3 block(TJ, TI);
+  if (df64) {
+    if (g.actx)
+      k_AAt_df<1><<<grid, block, 0, s>>>(g, kc, p, q, partials, sc, mode);
+    else
+      k_AAt_df<0><<<grid, block, 0, s>>>(g, kc, p, q, partials, sc, mode);
+    return;
+  }
   if (g.actx)
     k_AAt<1><<<grid, block, 0, s>>>(g, kc, p, q, partials, sc, mode);
   else

@@ -77,7 +77,7 @@ int validate_problem(const mfg_problem& p, int idx) {
   if (!(p.nu >= 0.0)) return set_error(MFG_ERR_INVALID_ARG, "nu must be >= 0" + at);
   if (!(p.f_a >= 0.0) || !(p.f_b >= 0.0) || !(p.g_a >= 0.0))
     return set_error(MFG_ERR_INVALID_ARG, "f_a, f_b, g_a must be >= 0 (monotone couplings)" + at);
-  if (p.l != 1 && p.l != 2) return set_error(MFG_ERR_INVALID_ARG, "l must be 1 or 2" + at);
+  if (p.l != 0 && p.l != 1 && p.l != 2) return set_error(MFG_ERR_INVALID_ARG, "l must be 0, 1 or 2" + at);
   if (!(p.gamma > 0.0) || !(p.tau0 > 0.0) || !(p.sigma0 > 0.0))
     return set_error(MFG_ERR_INVALID_ARG, "gamma, tau0, sigma0 must be > 0" + at);
   if (p.max_cp < 0 || p.max_cg < 1) return set_error(MFG_ERR_INVALID_ARG, "max_cp >= 0, max_cg >= 1" + at);
@@ -85,8 +85,8 @@ int validate_problem(const mfg_problem& p, int idx) {
     return set_error(MFG_ERR_INVALID_ARG, "cg_rule must be MFG_CG_FIXED or MFG_CG_ADAPTIVE" + at);
   if (p.cg_rule == MFG_CG_FIXED && !(p.cg_tol > 0.0))
     return set_error(MFG_ERR_INVALID_ARG, "cg_tol must be > 0" + at);
-  if (p.precision != MFG_FP64 && p.precision != MFG_MIXED)
-    return set_error(MFG_ERR_INVALID_ARG, "precision must be MFG_FP64 or MFG_MIXED" + at);
+  if (p.precision != MFG_FP64 && p.precision != MFG_MIXED && p.precision != MFG_MIXED_DF)
+    return set_error(MFG_ERR_INVALID_ARG, "precision must be MFG_FP64, MFG_MIXED or MFG_MIXED_DF" + at);
   const double nxy = (double)p.n[0] * (p.dim == 2 ? p.n[1] : 1);
   if (nxy * p.nt > 4.0e9) return set_error(MFG_ERR_INVALID_ARG, "instance too large" + at);
   return MFG_OK;
@@ -193,7 +193,8 @@ int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, con
   CK(cudaGraphConditionalHandleCreate(&hg, body_cp, 0, 0));
 
   const Geom& g = in.g;
-  const int flex = in.p.precision == MFG_MIXED;
+  const int flex = in.p.precision != MFG_FP64;
+  const int dfa = in.p.precision == MFG_MIXED_DF;
   cudaStream_t s = pl->cap0;
   CK(cudaStreamBeginCaptureToGraph(s, body_cp, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   launch_apply_C(g, ybar, in.r, 1.0, m0, in.partials, in.sc, 1, s);
@@ -220,7 +221,7 @@ int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, con
   CK(cudaStreamBeginCaptureToGraph(s2, body_cg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   const PcgDot dot{in.r, in.q, in.partials, in.sc, flex};
   const PcgZr zr{z, in.r, in.pv, in.q, in.partials, in.sc};
-  launch_AAt(g, in.pv, in.q, in.partials, in.sc, 1, s2);
+  launch_AAt(g, in.pv, in.q, in.partials, in.sc, 1, s2, dfa);
   launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s2, &dot, &zr);
   launch_update_p(g.n, in.zp, in.pv, in.sc, hg, 1, s2);
   CK(cudaStreamEndCapture(s2, &body_cg));
@@ -257,7 +258,8 @@ int solve_eager(mfg_plan_t pl, const double* m0, const double* V, const double* 
   DevScalars hs;
   for (auto& in : pl->inst) {
     const Geom& g = in.g;
-    const int flex = in.p.precision == MFG_MIXED;
+    const int flex = in.p.precision != MFG_FP64;
+  const int dfa = in.p.precision == MFG_MIXED_DF;
     const double* m0b = m0 + in.field_off;
     const double* Vb = V + in.field_off;
     const double* Wb = W + in.field_off;
@@ -275,7 +277,7 @@ int solve_eager(mfg_plan_t pl, const double* m0, const double* V, const double* 
         if (hs.cg_done) break;
         const PcgDot dot{in.r, in.q, in.partials, in.sc, flex};
         const PcgZr zr{zb, in.r, in.pv, in.q, in.partials, in.sc};
-        launch_AAt(g, in.pv, in.q, in.partials, in.sc, 1, s);
+        launch_AAt(g, in.pv, in.q, in.partials, in.sc, 1, s, dfa);
         launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s, &dot, &zr);
         launch_update_p(g.n, in.zp, in.pv, in.sc, 0, 0, s);
         pl->launches += 2 + precond_step_kernel_count(g, in.tabs);
@@ -346,7 +348,7 @@ int mfg_plan(const mfg_problem* probs, int batch, mfg_plan_t* out) {
         cudaMalloc(&in.q, n * 8) != cudaSuccess || cudaMalloc(&in.zp, n * 8) != cudaSuccess ||
         cudaMalloc(&in.partials, npart * 8) != cudaSuccess)
       return bail(MFG_ERR_CUDA, "cudaMalloc failed for solver workspace");
-    if (in.p.precision == MFG_MIXED) {
+    if (in.p.precision != MFG_FP64) {
       if (cudaMalloc(&in.work32, 2 * n * 4) != cudaSuccess)
         return bail(MFG_ERR_CUDA, "cudaMalloc failed for FP32 workspace");
     }
@@ -521,7 +523,8 @@ int mfg_adjoint(mfg_plan_t pl, int b, const double* y, const double* z, const do
   h.cg_tol_fixed = tol;
   h.max_cg = max_iter;
   CK(cudaMemcpyAsync(in.sc, &h, sizeof(h), cudaMemcpyHostToDevice, s));
-  const int flex = in.p.precision == MFG_MIXED;
+  const int flex = in.p.precision != MFG_FP64;
+  const int dfa = in.p.precision == MFG_MIXED_DF;
   // right-hand side C H^{-1} g; eta starts at 0
   launch_hinv(g, in.cf, y, gy, in.adj_t, s);
   launch_apply_C(g, in.adj_t, in.r, 1.0, nullptr, in.partials, in.sc, 3, s);
@@ -589,7 +592,7 @@ int mfg_apply_AAt(mfg_plan_t pl, int b, const double* p, double* q, void* stream
   if (rc != MFG_OK) return rc;
   if (!p || !q || p == q) return fail(MFG_ERR_INVALID_ARG, "p and q must be distinct non-null arrays");
   Inst& in = pl->inst[b];
-  launch_AAt(in.g, p, q, in.partials, in.sc, 0, (cudaStream_t)stream);
+  launch_AAt(in.g, p, q, in.partials, in.sc, 0, (cudaStream_t)stream, in.p.precision == MFG_MIXED_DF);
   pl->launches += 1;
   CK(cudaGetLastError());
   return MFG_OK;

@@ -74,8 +74,9 @@ void launch_apply_C(const Geom& g, const double* v, double* r, double alpha, con
                     double* partials, DevScalars* sc, int mode, cudaStream_t s,
                     const double* pdot = nullptr);
 void launch_apply_Ct(const Geom& g, const double* p, double* x, cudaStream_t s);
+// df64 != 0 selects the double-float variant of the stencil (MFG_MIXED_DF).
 void launch_AAt(const Geom& g, const double* p, double* q, double* partials, DevScalars* sc,
-                int mode, cudaStream_t s);
+                int mode, cudaStream_t s, int df64 = 0);
 int aat_blocks(const Geom& g);
 
 // Vector kernels (k_cg.cu).
@@ -99,6 +100,10 @@ struct PrecTables {
   // dct (N complex) per axis, both precisions.
   double *twx64 = nullptr, *dctx64 = nullptr, *twy64 = nullptr, *dcty64 = nullptr;
   float *twx32 = nullptr, *dctx32 = nullptr, *twy32 = nullptr, *dcty32 = nullptr;
+  // l = 0 (exact time solve): Thomas factors c_k(s), 1/den_k(s) (n each) and
+  // the off-diagonal per mode (S); null otherwise.
+  double *thc64 = nullptr, *thd64 = nullptr, *tho64 = nullptr;
+  float *thc32 = nullptr, *thd32 = nullptr, *tho32 = nullptr;
 };
 int build_prec_tables(const mfg_problem& p, const Geom& g, PrecTables* t, std::string* err);
 void free_prec_tables(PrecTables* t);

@@ -127,6 +127,8 @@ extern "C" int mfg_apply_precond_noalloc(const mfg_problem* p, const double* r, 
     return set_error(MFG_ERR_INVALID_ARG, "problem, r and z must be non-null and r != z");
   int rc = validate_problem(*p, 0);
   if (rc != MFG_OK) return rc;
+  if (p->l == 0)
+    return set_error(MFG_ERR_UNSUPPORTED, "mfg_apply_precond_noalloc: l = 0 needs plan-built factors");
   const Geom g = make_geom(*p);
   if (g.n > kNaMaxN || g.nx > kNaMaxAxis || g.ny > kNaMaxAxis || g.nt > kNaMaxNt)
     return set_error(MFG_ERR_INVALID_ARG,
@@ -152,7 +154,7 @@ extern "C" int mfg_apply_precond_noalloc(const mfg_problem* p, const double* r, 
   PrecTables t{};
   const long long ntab = (long long)g.nx * g.nx + (long long)g.ny * g.ny + (long long)g.nt * g.nt + g.nt + g.S;
   const int nb = (int)std::min<long long>((ntab + kThreads - 1) / kThreads, 1024);
-  if (p->precision == MFG_MIXED) {
+  if (p->precision == MFG_MIXED || p->precision == MFG_MIXED_DF) {
     float* w0 = nullptr;
     carve<float>(base, g, &t, &w0);
     k_noalloc_tables<float><<<nb, kThreads, 0, s>>>(g, p->l, t.Hx32, t.Hy32, t.Vt32, t.lamt32, t.L1_32, t.L2_32);

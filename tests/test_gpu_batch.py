@@ -40,7 +40,7 @@ def _solve(insts, iters, precision):
     return outs
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_df"])
 def test_batch_matches_solo_and_oracle(precision):
     insts = [mi.small(**c) for c in BATCH]
     iters = 15

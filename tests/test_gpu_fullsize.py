@@ -30,11 +30,13 @@ def test_fullsize_AAt_and_precond(which):
     n = ops.sizes(p)[1]
     L = lib()
     pv = mi.random_field(n, 51)
-    plan = L.mfg_plan(p, precision="fp64")
-    q = torch.empty(n, dtype=torch.float64, device="cuda")
-    L.mfg_apply_AAt(plan, 0, dev(pv), q)
-    torch.cuda.synchronize()
-    assert rel(host(q), solvers.apply_AAt_modal(p, pv)) <= 1e-11
+    ref_q = solvers.apply_AAt_modal(p, pv)
+    for prec in ("fp64", "mixed_df"):
+        plan = L.mfg_plan(p, precision=prec)
+        q = torch.empty(n, dtype=torch.float64, device="cuda")
+        L.mfg_apply_AAt(plan, 0, dev(pv), q)
+        torch.cuda.synchronize()
+        assert rel(host(q), ref_q) <= 1e-11, prec
     r = mi.random_field(n, 52)
     for prec, eta_max in (("fp64", 1e-12), ("mixed", 5e-5)):
         plan = L.mfg_plan(p, precision=prec)
@@ -71,7 +73,7 @@ def test_fullsize_prox_sampled(which):
     assert np.abs(flat(got)[:, cells] - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_df"])
 def test_fullsize_cp_config2(precision):
     """Three CP iterations on the 128^2 x 64 workload (nu = 1e-2) against the
     oracle; cond(AAt) ~ 1e6 here, so the bound is 1e-8."""

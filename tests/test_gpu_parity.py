@@ -85,11 +85,18 @@ def test_apply_C_Ct_AAt(case):
     for got, ref in ((host(r), ref_r), (host(x), ref_x), (host(q), ref_q)):
         assert rel(got, ref) <= 1e-12
         assert linf_rel(got, ref) <= 1e-12
+    # the double-float stencil (about 48 significant bits) of MFG_MIXED_DF
+    plan_df = _plan(p, "mixed_df")
+    L.mfg_apply_AAt(plan_df, 0, dev(pv), q)
+    torch.cuda.synchronize()
+    assert rel(host(q), ref_q) <= 1e-12
+    assert linf_rel(host(q), ref_q) <= 1e-12
 
 
 @pytest.mark.parametrize("case", CASES + POW2)
-@pytest.mark.parametrize("l", [1, 2])
+@pytest.mark.parametrize("l", [0, 1, 2])
 def test_precond_fp64(case, l):
+    """l = 1, 2: the paper's P (eq. prec); l = 0: the exact variant, P = AAt."""
     import torch
     inst = _inst(case, l=l)
     p = inst["problem"]
@@ -99,7 +106,7 @@ def test_precond_fp64(case, l):
     z = torch.empty(n, dtype=torch.float64, device="cuda")
     lib().mfg_apply_precond(plan, 0, dev(r), z)
     torch.cuda.synchronize()
-    P = ops.precond(p)
+    P = ops.AAt(p) if l == 0 else ops.precond(p)
     zg = host(z)
     assert _backward_error(P, zg, r) <= 1e-12
     assert rel(zg, solvers.solve_direct(P, r)) <= 1e-6
@@ -154,7 +161,7 @@ def _gpu_cp(inst, iters, precision="fp64", cg_tol=1e-10):
 
 
 @pytest.mark.parametrize("case", CASES + POW2[:3])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_df"])
 def test_cp_iterate(case, precision):
     """PCG at 1e-12 so that the comparison isolates the implementation.
 
@@ -197,7 +204,7 @@ def test_cp_resume_matches_single_run():
     assert rel(host(y), y2) <= 1e-13
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_df"])
 def test_config1_fixed_count(precision):
     """1-D periodic workload, 300 CP iterations, PCG at 1e-10: iterate vs oracle."""
     inst = mi.config1()
@@ -256,3 +263,22 @@ def test_problem1_shape_adaptive_tolerance():
     assert st[0].r_last <= p["cp_tol"]
     n = ops.sizes(p)[1]
     assert rel(host(y)[:n], ref["y"][0]) <= 1e-3
+
+
+@pytest.mark.parametrize("case", CASES[:2] + POW2[:2])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cp_exact_time_solve(case, precision):
+    """l = 0: the preconditioner is AAt itself (tridiagonal solves in time per
+    spatial mode), so FP64 PCG stops after one iteration and the CP iterate
+    matches the oracle like the paper's preconditioner does."""
+    inst = _inst(case, l=0)
+    p = inst["problem"]
+    iters = 15
+    rc, st, y, ybar, z = _gpu_cp(inst, iters, precision, cg_tol=1e-12)
+    assert rc == 0 and st.status == 0
+    if precision == "fp64":
+        assert st.max_cg_in_solve <= 2
+    ref = Solver(dict(p, l=1), inst["m0"], inst["V"], inst["W"], method="modal").run(inst["y0"], iters=iters)
+    ev = np.linalg.eigvalsh(ops.AAt(p).toarray())
+    tol = max(1e-8, 10 * (ev.max() / ev.min()) * 2.0 ** -53)
+    assert rel(y, ref["y"]) <= tol
