@@ -1,7 +1,7 @@
 // Space-time stencils of the discrete Fokker-Planck constraint:
 //   C v      (eq. ABC, reduced), the CP right-hand side sigma (C ybar - d),
 //   C^T p    (its transpose),
-//   C C^T p  (eq. largeA), fused in one pass over p.
+//   C C^T p  (eq. largeA), in two halo-free passes over p.
 //
 // Row k of C (plane k, time level k+1) reads
 //   L m^{k+1} - m^k/dt + div_h w^k,  L = nu K + I/dt   (Sec. 3, matrices A, B)
@@ -10,6 +10,8 @@
 // entries past the ends; on a periodic axis indices wrap.  Both cases use one
 // rule: a point has a "minus" neighbour (hm) and a "plus" neighbour (hp) unless
 // it sits at the matching end of a Neumann axis.
+#include <algorithm>
+
 #include "df64.cuh"
 #include "mfg_internal.cuh"
 #include "reduce.cuh"
@@ -184,151 +186,118 @@ void launch_apply_Ct(const Geom& g, const double* p, double* x, cudaStream_t s) 
 }
 
 // ---------------------------------------------------------------- C C^T p --
-// Fused factored form q = C (C^T p), marching in time over a chunk of planes.
-// With xm^k = L p^k - p^{k+1}/dt and B B^T = 2K (eq. precstead):
+// Factored form q = C (C^T p).  With xm^k = L p^k - p^{k+1}/dt (the m rows of
+// C^T p) and B B^T = 2K (eq. precstead):
 //   q^k = L xm^k - xm^{k-1}/dt + 2 K p^k        (xm^{-1} := 0).
-// A block owns a TI x TJ spatial tile; p planes are staged in shared memory
-// with a 2-point halo, xm with a 1-point halo.  Each p plane is read from
-// global memory once per tile (plus halo) instead of once per stencil point.
 //
-// FP64 issue is the limit on GB300 (1/58 of the FP32 rate), so the stencil is
-// branch-free with the fewest FP64 instructions:
-//   K u = cK u - ax (uW + uE) - ay (uN + uS),   cK = 2 (ax + ay),
-// (5 FP64 ops; nu folded into the coefficients where only nu K u is needed).
-// On a Neumann axis the halos hold mirror images (u_{-1} = u_0, u_N = u_{N-1}),
-// which turns the same formula into the one-sided D^1 (D^1)^T rows of Sec. 4.3;
-// xm halo slots outside the domain are refreshed from their mirrors after xm is
-// formed.
-constexpr int TI = 16, TJ = 32;
-constexpr int H2I = TI + 4, H2J = TJ + 4;  // p tile with halo 2
-constexpr int H1I = TI + 2, H1J = TJ + 2;  // xm tile with halo 1
+// FP64 issue is the limit on GB300 (a warp's FP64 instruction takes 16 SM
+// clocks; memory traffic is far below the HBM bound), so the stencil is laid
+// out for the fewest FP64 instructions per point:
+//   K u = cK u - ax (uW + uE) - ay (uN + uS),   cK = 2 (ax + ay)   (5 ops),
+// and it runs in two halo-free passes over the grid, each point computed once:
+//   pass 1:  kp = K p,   X = dt xm = fma(nu dt, kp, p^k - p^{k+1})        (7 ops)
+//   pass 2:  q = c4 X - c2 (XW + XE) - c1 (XN + XS) - X^{k-1}/dt^2 + 2 kp (7 ops)
+// with c1 = nu ay/dt, c2 = nu ax/dt, c4 = nu cK/dt + 1/dt^2, plus one FMA for
+// p.q.  (A one-pass version that forms xm on a shared-memory tile must
+// recompute it on the tile's halo and needs ~20 FP64 ops per point.)
+// On a Neumann axis the neighbour index of an end point is the point itself
+// (u_{-1} = u_0, u_N = u_{N-1}), which turns the same formula into the
+// one-sided D^1 (D^1)^T rows of Sec. 4.3, for p and for X alike.
+// Threads own one (i, j) column and march over a chunk of time planes, so
+// p^{k+1} and X^{k-1} stay in registers from one plane to the next.
+constexpr int AJ = 32, AI = 8;  // block = AJ x AI columns
 
-int aat_chunk(const Geom& g) {
-  const long long tiles = (long long)((g.ny + TJ - 1) / TJ) * ((g.nx + TI - 1) / TI);
-  long long want = 152 * 4;
-  long long chunks = (want + tiles - 1) / tiles;
+struct AatCoef {
+  double ax, ay, cK, ndt;      // pass 1
+  double c1, c2, c4, idt2;     // pass 2
+};
+
+AatCoef aat_coef(const Geom& g) {
+  const double ax = g.actx ? g.ax : 0.0, ay = g.ay, cK = 2.0 * (ax + ay);
+  const double dt = 1.0 / g.idt, idt2 = g.idt * g.idt;
+  return AatCoef{ax, ay, cK, g.nu * dt, g.nu * ay * g.idt, g.nu * ax * g.idt, g.nu * cK * g.idt + idt2, idt2};
+}
+
+int aat2_chunk(const Geom& g) {
+  const long long cols = (long long)((g.ny + AJ - 1) / AJ) * ((g.nx + AI - 1) / AI);
+  const long long want = 152 * 8;  // 256-thread blocks: 8 per SM fill it
+  long long chunks = (want + cols - 1) / cols;
   if (chunks < 1) chunks = 1;
   if (chunks > g.nt) chunks = g.nt;
-  int kc = (int)((g.nt + chunks - 1) / chunks);
-  if (kc < 2) kc = 2;
-  if (kc > g.nt) kc = g.nt;
-  return kc;
+  return (int)((g.nt + chunks - 1) / chunks);
 }
 
-int aat_blocks(const Geom& g) {
-  const int kc = aat_chunk(g);
-  return ((g.ny + TJ - 1) / TJ) * ((g.nx + TI - 1) / TI) * ((g.nt + kc - 1) / kc);
+dim3 aat2_grid(const Geom& g, int kc) {
+  return dim3((g.ny + AJ - 1) / AJ, (g.nx + AI - 1) / AI, (g.nt + kc - 1) / kc);
 }
 
-// Index of grid point i on an axis: wrapped when periodic, mirrored across the
-// end when Neumann (i = -1 -> 0, -2 -> 1, N -> N-1, N+1 -> N-2).
-__device__ __forceinline__ int halo_index(int i, int N, int per) {
-  if (i >= 0 && i < N) return i;
-  if (per) {
-    i %= N;
-    return i < 0 ? i + N : i;
-  }
-  int m = i < 0 ? -1 - i : 2 * N - 1 - i;
-  return m < 0 ? 0 : (m >= N ? N - 1 : m);
-}
+struct Cols {
+  int jm, jp, im, ip;
+};
 
-__device__ __forceinline__ void load_plane_h2(const Geom& g, const double* __restrict__ p, int k,
-                                              int i0, int j0, double (*dst)[H2J]) {
-  const int tid = threadIdx.x + TJ * threadIdx.y;
-  if (k >= g.nt) {
-    for (int s = tid; s < H2I * H2J; s += TI * TJ) dst[s / H2J][s % H2J] = 0.0;
-    return;
-  }
-  const double* pk = p + (long long)k * g.S;
-  for (int s = tid; s < H2I * H2J; s += TI * TJ) {
-    const int li = s / H2J, lj = s % H2J;
-    const int gi = halo_index(i0 + li - 2, g.nx, g.perx);
-    const int gj = halo_index(j0 + lj - 2, g.ny, g.pery);
-    dst[li][lj] = pk[(long long)gi * g.ny + gj];
-  }
-}
-
-template <int ACTX, int WID>
-__device__ __forceinline__ double fast_K(const double (*A)[WID], int r, int c, double ax, double ay,
-                                         double cK) {
-  double t = ay * (A[r][c - 1] + A[r][c + 1]);
-  if (ACTX) t = fma(ax, A[r - 1][c] + A[r + 1][c], t);
-  return fma(cK, A[r][c], -t);
+// Neighbour columns: wrapped on a periodic axis, the point itself at the end
+// of a Neumann axis (and on an axis of length 1).
+__device__ __forceinline__ Cols aat_cols(const Geom& g, int i, int j) {
+  Cols c;
+  c.jm = j == 0 ? (g.pery ? g.ny - 1 : 0) : j - 1;
+  c.jp = j == g.ny - 1 ? (g.pery ? 0 : g.ny - 1) : j + 1;
+  c.im = i == 0 ? (g.perx ? g.nx - 1 : 0) : i - 1;
+  c.ip = i == g.nx - 1 ? (g.perx ? 0 : g.nx - 1) : i + 1;
+  return c;
 }
 
 template <int ACTX>
-__global__ void __launch_bounds__(TI * TJ, 2) k_AAt(Geom g, int kc, const double* __restrict__ p,
-                                                    double* __restrict__ q, double* partials,
-                                                    DevScalars* sc, int mode) {
+__global__ void __launch_bounds__(AJ * AI) k_aat_x(Geom g, AatCoef a, int kc, const double* __restrict__ p,
+                                                   double* __restrict__ X, double* __restrict__ KP,
+                                                   const DevScalars* sc, int mode) {
   if (mode == 1 && sc->cg_done) return;
-  __shared__ double P[2][H2I][H2J];
-  __shared__ double XM[H1I][H1J];
-  __shared__ double KP[TI][TJ];
-  const int tj = threadIdx.x, ti = threadIdx.y;
-  const int j0 = blockIdx.x * TJ, i0 = blockIdx.y * TI;
-  const int k0 = blockIdx.z * kc;
-  const int k1 = min(g.nt, k0 + kc);
-  const int gi = i0 + ti, gj = j0 + tj;
-  const bool own = gi < g.nx && gj < g.ny;
-  const double ax = ACTX ? g.ax : 0.0, ay = g.ay, cK = 2.0 * (ax + ay);
-  const double nax = g.nu * ax, nay = g.nu * ay, ncK = g.nu * cK;
-  // xm halo slots that lie outside a Neumann axis (rebuilt from their mirrors)
-  const bool ghost_x = ACTX && !g.perx && (i0 == 0 || i0 + TI >= g.nx);
-  const bool ghost_y = !g.pery && (j0 == 0 || j0 + TJ >= g.ny);
-  const bool ghosts = ghost_x || ghost_y;
-  const int tid = tj + TJ * ti;
-
-  int cur = 0;
-  load_plane_h2(g, p, k0, i0, j0, P[cur]);
-  double xprev = 0.0;
-  if (k0 > 0) {
-    load_plane_h2(g, p, k0 - 1, i0, j0, P[cur ^ 1]);
-    __syncthreads();
-    if (own)
-      xprev = fast_K<ACTX, H2J>(P[cur ^ 1], ti + 2, tj + 2, nax, nay, ncK) +
-              (P[cur ^ 1][ti + 2][tj + 2] - P[cur][ti + 2][tj + 2]) * g.idt;
-    __syncthreads();
-  }
-  double acc = 0.0;
+  const int j = blockIdx.x * AJ + threadIdx.x, i = blockIdx.y * AI + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  const int k0 = blockIdx.z * kc, k1 = min(g.nt, k0 + kc);
+  const Cols nb = aat_cols(g, i, j);
+  const long long row = (long long)i * g.ny;
+  long long base = (long long)k0 * g.S;
+  double c = p[base + row + j];
   for (int k = k0; k < k1; ++k) {
-    load_plane_h2(g, p, k + 1, i0, j0, P[cur ^ 1]);
-    __syncthreads();
-    const double (*Pk)[H2J] = P[cur];
-    const double (*Pn)[H2J] = P[cur ^ 1];
-    // One FP64 sequence for every slot (no divergent paths): K p, then xm.
-    for (int s = tid; s < H1I * H1J; s += TI * TJ) {
-      const int li = s / H1J, lj = s % H1J;
-      const double kp = fast_K<ACTX, H2J>(Pk, li + 1, lj + 1, ax, ay, cK);
-      XM[li][lj] = fma(g.nu, kp, (Pk[li + 1][lj + 1] - Pn[li + 1][lj + 1]) * g.idt);
-      if (li >= 1 && li <= TI && lj >= 1 && lj <= TJ) KP[li - 1][lj - 1] = kp;
+    const double pn = (k + 1 < g.nt) ? p[base + g.S + row + j] : 0.0;
+    double t = a.ay * (p[base + row + nb.jm] + p[base + row + nb.jp]);
+    if (ACTX) t = fma(a.ax, p[base + (long long)nb.im * g.ny + j] + p[base + (long long)nb.ip * g.ny + j], t);
+    const double kp = fma(a.cK, c, -t);
+    X[base + row + j] = fma(a.ndt, kp, c - pn);
+    KP[base + row + j] = kp;
+    c = pn;
+    base += g.S;
+  }
+}
+
+// mode 0: q = AAt p.  mode 1 (PCG step): also reduces p.q and sets
+// alpha = rz/(p.q) in the device scalars.
+template <int ACTX>
+__global__ void __launch_bounds__(AJ * AI) k_aat_q(Geom g, AatCoef a, int kc, const double* __restrict__ X,
+                                                   const double* __restrict__ KP, const double* __restrict__ p,
+                                                   double* __restrict__ q, double* partials, DevScalars* sc,
+                                                   int mode) {
+  if (mode == 1 && sc->cg_done) return;
+  const int j = blockIdx.x * AJ + threadIdx.x, i = blockIdx.y * AI + threadIdx.y;
+  double acc = 0.0;
+  if (i < g.nx && j < g.ny) {
+    const int k0 = blockIdx.z * kc, k1 = min(g.nt, k0 + kc);
+    const Cols nb = aat_cols(g, i, j);
+    const long long row = (long long)i * g.ny;
+    long long base = (long long)k0 * g.S;
+    double xprev = k0 > 0 ? X[base - g.S + row + j] : 0.0;
+    for (int k = k0; k < k1; ++k) {
+      const double xc = X[base + row + j];
+      double t = a.c1 * (X[base + row + nb.jm] + X[base + row + nb.jp]);
+      if (ACTX) t = fma(a.c2, X[base + (long long)nb.im * g.ny + j] + X[base + (long long)nb.ip * g.ny + j], t);
+      t = fma(a.idt2, xprev, t);
+      t = fma(-2.0, KP[base + row + j], t);
+      const double qv = fma(a.c4, xc, -t);
+      q[base + row + j] = qv;
+      if (mode == 1) acc = fma(qv, p[base + row + j], acc);
+      xprev = xc;
+      base += g.S;
     }
-    __syncthreads();
-    if (ghosts) {
-      for (int s = tid; s < H1I * H1J; s += TI * TJ) {
-        const int li = s / H1J, lj = s % H1J;
-        const int xi = i0 + li - 1, xj = j0 + lj - 1;
-        const bool ox = ghost_x && (xi < 0 || xi >= g.nx);
-        const bool oy = ghost_y && (xj < 0 || xj >= g.ny);
-        if (ox || oy) {
-          const int mi = ox ? (xi < 0 ? li + 1 : li - 1) : li;
-          const int mj = oy ? (xj < 0 ? lj + 1 : lj - 1) : lj;
-          // mirror slot is inside the domain (read-only here: distinct from ghosts)
-          XM[li][lj] = XM[mi][mj];
-        }
-      }
-      __syncthreads();
-    }
-    if (own) {
-      const double c = XM[ti + 1][tj + 1];
-      const double nKxm = fast_K<ACTX, H1J>(XM, ti + 1, tj + 1, nax, nay, ncK);
-      const double val = fma(2.0, KP[ti][tj], fma(c - xprev, g.idt, nKxm));
-      xprev = c;
-      const long long e = (long long)k * g.S + (long long)gi * g.ny + gj;
-      q[e] = val;
-      acc = fma(val, Pk[ti + 2][tj + 2], acc);
-    }
-    __syncthreads();
-    cur ^= 1;
   }
   if (mode != 1) return;
   double part[1] = {acc};
@@ -349,9 +318,50 @@ __global__ void __launch_bounds__(TI * TJ, 2) k_AAt(Geom g, int kc, const double
   }
 }
 
-// The same fused stencil in double-float arithmetic (df64.cuh): p is split into
-// FP32 pairs as it is staged, every stencil operation runs on FP32 pairs, and q
-// is rebuilt in FP64 (one FP64 add per point) together with the FP64 p.q.
+// Fused one-pass stencil on shared-memory tiles, used by the double-float
+// variant: a block owns a TI x TJ spatial tile and marches over a chunk of
+// planes; p planes are staged with a 2-point halo, xm with a 1-point halo (on
+// a Neumann axis the halos hold mirror images; xm halo slots outside the
+// domain are refreshed from their mirrors after xm is formed).
+constexpr int TI = 16, TJ = 32;
+constexpr int H2I = TI + 4, H2J = TJ + 4;  // p tile with halo 2
+constexpr int H1I = TI + 2, H1J = TJ + 2;  // xm tile with halo 1
+
+int aat_chunk(const Geom& g) {
+  const long long tiles = (long long)((g.ny + TJ - 1) / TJ) * ((g.nx + TI - 1) / TI);
+  long long want = 152 * 4;
+  long long chunks = (want + tiles - 1) / tiles;
+  if (chunks < 1) chunks = 1;
+  if (chunks > g.nt) chunks = g.nt;
+  int kc = (int)((g.nt + chunks - 1) / chunks);
+  if (kc < 2) kc = 2;
+  if (kc > g.nt) kc = g.nt;
+  return kc;
+}
+
+int aat_blocks(const Geom& g) {
+  const int kc = aat_chunk(g);
+  const long long one = (long long)((g.ny + TJ - 1) / TJ) * ((g.nx + TI - 1) / TI) * ((g.nt + kc - 1) / kc);
+  const dim3 g2 = aat2_grid(g, aat2_chunk(g));
+  const long long two = (long long)g2.x * g2.y * g2.z;
+  return (int)std::max(one, two);
+}
+
+// Index of grid point i on an axis: wrapped when periodic, mirrored across the
+// end when Neumann (i = -1 -> 0, -2 -> 1, N -> N-1, N+1 -> N-2).
+__device__ __forceinline__ int halo_index(int i, int N, int per) {
+  if (i >= 0 && i < N) return i;
+  if (per) {
+    i %= N;
+    return i < 0 ? i + N : i;
+  }
+  int m = i < 0 ? -1 - i : 2 * N - 1 - i;
+  return m < 0 ? 0 : (m >= N ? N - 1 : m);
+}
+
+// The double-float version (df64.cuh): p is split into FP32 pairs as it is
+// staged, every stencil operation runs on FP32 pairs, and q is rebuilt in FP64
+// (one FP64 add per point) together with the FP64 p.q.
 // About 48 significant bits; used by the MFG_MIXED_DF precision.
 __device__ __forceinline__ void load_plane_h2_df(const Geom& g, const double* __restrict__ p, int k,
                                                  int i0, int j0, df (*dst)[H2J]) {
@@ -470,22 +480,32 @@ __global__ void __launch_bounds__(TI * TJ, 2) k_AAt_df(Geom g, int kc, const dou
   }
 }
 
-void launch_AAt(const Geom& g, const double* p, double* q, double* partials, DevScalars* sc,
-                int mode, cudaStream_t s, int df64) {
-  const int kc = aat_chunk(g);
-  dim3 grid((g.ny + TJ - 1) / TJ, (g.nx + TI - 1) / TI, (g.nt + kc - 1) / kc);
-  dim3 block(TJ, TI);
+void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, double* partials,
+                DevScalars* sc, int mode, cudaStream_t s, int df64) {
   if (df64) {
+    const int kc = aat_chunk(g);
+    dim3 grid((g.ny + TJ - 1) / TJ, (g.nx + TI - 1) / TI, (g.nt + kc - 1) / kc);
+    dim3 block(TJ, TI);
     if (g.actx)
       k_AAt_df<1><<<grid, block, 0, s>>>(g, kc, p, q, partials, sc, mode);
     else
       k_AAt_df<0><<<grid, block, 0, s>>>(g, kc, p, q, partials, sc, mode);
     return;
   }
-  if (g.actx)
-    k_AAt<1><<<grid, block, 0, s>>>(g, kc, p, q, partials, sc, mode);
-  else
-    k_AAt<0><<<grid, block, 0, s>>>(g, kc, p, q, partials, sc, mode);
+  const AatCoef a = aat_coef(g);
+  const int kc = aat2_chunk(g);
+  const dim3 grid = aat2_grid(g, kc), block(AJ, AI);
+  double* X = scratch;
+  double* KP = scratch + g.n;
+  if (g.actx) {
+    k_aat_x<1><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
+    k_aat_q<1><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
+  } else {
+    k_aat_x<0><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
+    k_aat_q<0><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
+  }
 }
+
+int aat_kernel_count(int df64) { return df64 ? 1 : 2; }
 
 }  // namespace mfg

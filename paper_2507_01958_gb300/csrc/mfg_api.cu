@@ -175,7 +175,9 @@ int check_b(mfg_plan_t pl, int b) {
 
 // kernels per CP iteration outside PCG (rhs, precond, init_p, arm, prox) and per PCG iteration
 int launches_cp(const Inst& in) { return 4 + precond_kernel_count(in.g); }
-int launches_cg(const Inst& in) { return 2 + precond_step_kernel_count(in.g, in.tabs); }
+int launches_cg(const Inst& in) {
+  return 1 + aat_kernel_count(in.p.precision == MFG_MIXED_DF) + precond_step_kernel_count(in.g, in.tabs);
+}
 
 // Captures the per-instance CP loop into `top` as a while-node branch.
 int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, const double* V,
@@ -221,7 +223,7 @@ int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, con
   CK(cudaStreamBeginCaptureToGraph(s2, body_cg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   const PcgDot dot{in.r, in.q, in.partials, in.sc, flex};
   const PcgZr zr{z, in.r, in.pv, in.q, in.partials, in.sc};
-  launch_AAt(g, in.pv, in.q, in.partials, in.sc, 1, s2, dfa);
+  launch_AAt(g, in.pv, in.q, in.work64, in.partials, in.sc, 1, s2, dfa);
   launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s2, &dot, &zr);
   launch_update_p(g.n, in.zp, in.pv, in.sc, hg, 1, s2);
   CK(cudaStreamEndCapture(s2, &body_cg));
@@ -277,10 +279,10 @@ int solve_eager(mfg_plan_t pl, const double* m0, const double* V, const double* 
         if (hs.cg_done) break;
         const PcgDot dot{in.r, in.q, in.partials, in.sc, flex};
         const PcgZr zr{zb, in.r, in.pv, in.q, in.partials, in.sc};
-        launch_AAt(g, in.pv, in.q, in.partials, in.sc, 1, s, dfa);
+        launch_AAt(g, in.pv, in.q, in.work64, in.partials, in.sc, 1, s, dfa);
         launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s, &dot, &zr);
         launch_update_p(g.n, in.zp, in.pv, in.sc, 0, 0, s);
-        pl->launches += 2 + precond_step_kernel_count(g, in.tabs);
+        pl->launches += launches_cg(in);
       }
       launch_prox_cp(g, in.cf, zb, yb, ybb, Vb, Wb, in.partials, in.sc, 0, 0, s);
       pl->launches += 1;
@@ -592,8 +594,8 @@ int mfg_apply_AAt(mfg_plan_t pl, int b, const double* p, double* q, void* stream
   if (rc != MFG_OK) return rc;
   if (!p || !q || p == q) return fail(MFG_ERR_INVALID_ARG, "p and q must be distinct non-null arrays");
   Inst& in = pl->inst[b];
-  launch_AAt(in.g, p, q, in.partials, in.sc, 0, (cudaStream_t)stream, in.p.precision == MFG_MIXED_DF);
-  pl->launches += 1;
+  launch_AAt(in.g, p, q, in.work64, in.partials, in.sc, 0, (cudaStream_t)stream, in.p.precision == MFG_MIXED_DF);
+  pl->launches += aat_kernel_count(in.p.precision == MFG_MIXED_DF);
   CK(cudaGetLastError());
   return MFG_OK;
 }

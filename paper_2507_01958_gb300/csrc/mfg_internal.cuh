@@ -75,8 +75,10 @@ void launch_apply_C(const Geom& g, const double* v, double* r, double alpha, con
                     const double* pdot = nullptr);
 void launch_apply_Ct(const Geom& g, const double* p, double* x, cudaStream_t s);
 // df64 != 0 selects the double-float variant of the stencil (MFG_MIXED_DF).
-void launch_AAt(const Geom& g, const double* p, double* q, double* partials, DevScalars* sc,
-                int mode, cudaStream_t s, int df64 = 0);
+// q = AAt p.  scratch: 2 n doubles (unused by the double-float variant).
+void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, double* partials,
+                DevScalars* sc, int mode, cudaStream_t s, int df64);
+int aat_kernel_count(int df64);
 int aat_blocks(const Geom& g);
 
 // Vector kernels (k_cg.cu).
