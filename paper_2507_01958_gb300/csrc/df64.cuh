@@ -40,7 +40,25 @@ __device__ __forceinline__ df df_add(df a, df b) {
   return quick_two_sum(s.hi, s.lo);
 }
 
+// a + b for operands of the same sign (no cancellation): the cheaper
+// "sloppy" addition, relative error ~2^-47.
+__device__ __forceinline__ df df_add_same(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
+// a + b with b a single FP32 number.
+__device__ __forceinline__ df df_add_f(df a, float b) {
+  const df s = two_sum(a.hi, b);
+  return quick_two_sum(s.hi, s.lo + a.lo);
+}
+
 __device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+
+// a < b, a <= b on the represented values (|lo| <= ulp(hi)/2 makes the pairs
+// ordered by hi first).
+__device__ __forceinline__ bool df_lt(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool df_le(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 
 // a * b: the exact product of the high parts by FMA, plus the cross terms.

@@ -15,21 +15,11 @@
 // Root finder: Newton from m = 0 with the bracket [lo, hi] kept by the sign of
 // h and a bisection step whenever Newton leaves it (for f_b = 0, h is concave
 // and Newton from the left never does); see prox_cell for the precision split.
+#include "df64.cuh"
 #include "mfg_internal.cuh"
 #include "reduce.cuh"
 
 namespace mfg {
-
-// 1/d in FP64 without the FP64 divide: an FP32 reciprocal seed refined by two
-// Newton-Raphson steps r <- r (2 - d r) (the classical reciprocal iteration;
-// each step squares the relative error, 1e-7 -> 1e-14 -> round-off).  Valid
-// for d in the FP32 normal range, which the callers check.
-__device__ __forceinline__ double rcp64(double d) {
-  double r = (double)(1.0f / (float)d);
-  r = fma(r, fma(-d, r, 1.0), r);
-  r = fma(r, fma(-d, r, 1.0), r);
-  return r;
-}
 
 // Safeguarded Newton on h in FP32, from x = 0 with the bracket [0, hi].
 __device__ __forceinline__ float newton_h32(float hi, float B, float hP, float tau, float a1, float tb) {
@@ -50,17 +40,65 @@ __device__ __forceinline__ float newton_h32(float hi, float B, float hP, float t
   return x;
 }
 
-// Root of h(m) = (1 + tau a) m + tau b m^2 - B - hP/(m + tau)^2 with
+// FP64 Newton on h from x = 0 with bisection safeguard: the path for inputs
+// outside the FP32 range of the fast path.
+__device__ __noinline__ double newton_h64(double B, double hP, double tau, double a1, double tb, double hi) {
+  double x = 0.0, lo = 0.0;
+  for (int it = 0; it < 200; ++it) {
+    const double it1 = 1.0 / (x + tau);
+    const double it2 = it1 * it1;
+    const double hx = fma(tb, x * x, a1 * x) - B - hP * it2;
+    if (hx < 0.0) lo = x; else hi = x;
+    if (hx == 0.0) break;
+    const double dh = fma(2.0 * tb, x, a1) + 2.0 * hP * it2 * it1;
+    double xn = x - hx / dh;
+    if (!(xn >= lo && xn <= hi)) xn = 0.5 * (lo + hi);
+    const double dxv = fabs(xn - x);
+    x = xn;
+    if (dxv <= 1e-16 * x || hi - lo <= 4e-16 * hi) break;
+  }
+  return x;
+}
+
+// Per-step constants of the prox (tau is the CP primal step).
+struct ProxK {
+  double tau, half_tau, half_itau, tb;  // tau, tau/2, 1/(2 tau), tau f_b
+  float tauf, tbf;
+  df taud, tbd;                         // tau, tau f_b as double-float pairs
+  bool tau_ok;                          // tau inside the FP32 fast-path range
+};
+
+__device__ __forceinline__ ProxK prox_consts(double tau, double f_b) {
+  ProxK k;
+  k.tau = tau;
+  k.half_tau = 0.5 * tau;
+  k.half_itau = 0.5 / tau;
+  k.tb = tau * f_b;
+  k.tauf = (float)tau;
+  k.tbf = (float)k.tb;
+  k.taud = df_from_double(tau);
+  k.tbd = df_from_double(k.tb);
+  k.tau_ok = tau > 1e-15 && tau < 1e15;
+  return k;
+}
+
+// Root of h(m) = a1 m + tau b m^2 - B - hP/(m + tau)^2 with a1 = 1 + tau a,
 // B = m_bar - tau c and hP = tau |P|^2 / 2 (the scalar equation above, with
-// the FP64 constants combined before any rounding to FP32).  FP64 runs at
-// about 1/58 of the FP32 rate on GB300, so the iteration runs in FP32 and FP64
-// Newton steps polish the result; the polish stops once a step is below
-// 1e-8 relative (quadratic convergence leaves ~1e-16) and keeps the bracket,
-// bisecting if a step leaves it.
+// the FP64 constants combined before any rounding), then w = m/(m + tau) P.
+// FP64 issues at 1/64 of the FP32 rate on GB300, so the root is found in FP32
+// and polished in double-float arithmetic (df64.cuh, ~48 bits) by Newton
+// steps on
+//   g(m) = h(m) (m + tau)^2 = (a1 m + tau b m^2 - B) (m + tau)^2 - hP,
+// which has the sign of h (the bracket stays valid) and needs no reciprocal;
+// g' = (a1 + 2 tau b m)(m + tau)^2 + 2 (a1 m + tau b m^2 - B)(m + tau) > 0 near
+// the root (there a1 m + tau b m^2 - B = hP/(m + tau)^2 >= 0) and is taken in
+// FP32, so each step shrinks the error by ~1e-7 (plus the quadratic term):
+// from an FP32 root two steps reach the double-float resolution.  The polish
+// stops after a step below 1e-9 relative and keeps the bracket, bisecting if
+// a step leaves it.  Inputs outside the FP32 range take an FP64 Newton.
 template <int NW>
-__device__ __forceinline__ void prox_cell(double mbar, const double (&wbar)[NW], double tau,
-                                          double inv_tau, double a, double b, double c, double& m,
-                                          double (&w)[NW]) {
+__device__ __forceinline__ void prox_cell(double mbar, const double (&wbar)[NW], const ProxK& K, double a1,
+                                          float a1f, const df& a1d, double c, double& m, double (&w)[NW]) {
   // projection onto K by sign tests on the bit patterns (no FP64 min/max)
   double P[NW];
   double P2 = 0.0;
@@ -70,51 +108,67 @@ __device__ __forceinline__ void prox_cell(double mbar, const double (&wbar)[NW],
     P[q] = ((q & 1) ? neg : !neg) ? wbar[q] : 0.0;
     P2 = fma(P[q], P[q], P2);
   }
-  const double B = mbar - tau * c;
-  const double half_P2_tau = 0.5 * P2 * inv_tau;
-  if (-B - half_P2_tau >= 0.0) {  // h(0) >= 0
+  const double B = fma(-K.tau, c, mbar);
+  const double hp0 = P2 * K.half_itau;  // |P|^2 / (2 tau)
+  if (B + hp0 <= 0.0) {                 // h(0) = -B - |P|^2/(2 tau) >= 0
     m = 0.0;
 #pragma unroll
     for (int q = 0; q < NW; ++q) w[q] = 0.0;
     return;
   }
-  double hi = (B > 0.0 ? B : 0.0) + half_P2_tau;
-  double lo = 0.0;
-  const double hP = 0.5 * tau * P2;
-  const double a1 = fma(tau, a, 1.0), tb = tau * b;
-  const bool fp32_ok = hi < 1e30 && hP < 1e30 && fabs(B) < 1e30 && tau > 1e-30 && tau < 1e30;
-  double x = 0.0;
-  // FP64 polish: from an FP32 root (relative error ~1e-7) one Newton step
-  // leaves ~1e-14; another step is taken only if the first moved by more than
-  // 2e-7 relative (an FP32 root spoiled by cancellation) or there was no FP32 root.
-  double stop = 2e-7;
-  if (fp32_ok) {
-    x = (double)newton_h32((float)hi, (float)B, (float)hP, (float)tau, (float)a1, (float)tb);
-  } else {
-    stop = 1e-8;
+  const double hi0 = fmax(B, 0.0) + hp0;
+  const double hP = K.half_tau * P2;
+  const float hif = (float)hi0, Bf = (float)B, hPf = (float)hP;
+  const bool fp32_ok = K.tau_ok && hif < 1e15f && hPf < 1e30f && fabsf(Bf) < 1e30f;
+  if (!fp32_ok) {
+    const double x = newton_h64(B, hP, K.tau, a1, K.tb, hi0);
+    m = x;
+    const double s = x / (x + K.tau);
+#pragma unroll
+    for (int q = 0; q < NW; ++q) w[q] = s * P[q];
+    return;
   }
+  const df Bd = df_from_double(B), hPd = df_from_double(hP);
+  df lo{0.0f, 0.0f}, hi = df_from_double(hi0);
+  df x{newton_h32(hif, Bf, hPf, K.tauf, a1f, K.tbf), 0.0f};
   for (int it = 0; it < 100; ++it) {
-    const double t = x + tau;
-    const double it1 = fp32_ok ? rcp64(t) : 1.0 / t;
-    const double it2 = it1 * it1;
-    const double hx = fma(tb, x * x, a1 * x) - B - hP * it2;
-    if (hx < 0.0) lo = x; else hi = x;
-    if (hx == 0.0) break;
-    const double dh = fma(2.0 * tb, x, a1) + 2.0 * hP * it2 * it1;
-    double xn = x - hx * ((fp32_ok && dh < 1e37) ? rcp64(dh) : 1.0 / dh);
-    if (!(xn >= lo && xn <= hi)) xn = 0.5 * (lo + hi);
-    const double dxv = fabs(xn - x);
-    x = xn;
-    if (dxv <= stop * x || hi - lo <= 4e-16 * hi) break;
-    stop = 1e-8;
+    const df t = df_add_same(x, K.taud);
+    const df t2 = df_mul(t, t);
+    const df u = df_add_same(df_mul(K.tbd, x), a1d);  // a1 + tau b x
+    const df v = df_sub(df_mul(u, x), Bd);            // a1 x + tau b x^2 - B
+    const df gx = df_sub(df_mul(v, t2), hPd);
+    if (gx.hi < 0.0f) lo = x; else hi = x;
+    if (gx.hi == 0.0f) break;
+    const float dg = fmaf(fmaf(2.0f * K.tbf, x.hi, a1f), t2.hi, 2.0f * v.hi * t.hi);
+    const float dx = __fdiv_rn(gx.hi, dg);
+    const df xn = df_add_f(x, -dx);
+    if (df_le(lo, xn) && df_le(xn, hi)) {
+      x = xn;
+      if (fabsf(dx) <= 1e-9f * x.hi) break;
+    } else {
+      const df mid = df_add_same(lo, hi);
+      x = df{0.5f * mid.hi, 0.5f * mid.lo};
+      if (df_sub(hi, lo).hi <= 1e-14f * hi.hi) break;
+    }
   }
-  m = x;
-  const double s = x * (fp32_ok ? rcp64(x + tau) : 1.0 / (x + tau));
+  // s = x / (x + tau): FP32 reciprocal refined once in double-float
+  const df t = df_add_same(x, K.taud);
+  const float r0 = __frcp_rn(t.hi);
+  const df e = df_sub(df{1.0f, 0.0f}, df_mul(t, df{r0, 0.0f}));  // 1 - t r0, ~1e-7
+  const df r = df_add_f(df{r0 * e.hi, 0.0f}, r0);                // r0 (1 + e)
+  m = df_to_double(x);
+  const double s = df_to_double(df_mul(x, r));
 #pragma unroll
   for (int q = 0; q < NW; ++q) w[q] = s * P[q];
 }
 
 // y, ybar hold c planes; z one plane set.  Cell e pairs (m^{k+1}, w^k).
+// The lift x = C^T z is formed from the four one-sided differences of z, which
+// serve both the fluxes (x_w = D^T-type differences / dx) and
+//   K z = ax ((z - zE) - (zW - z)) + ay ((z - zN) - (zS - z));
+// on a Neumann axis the neighbour index of an end point is the point itself,
+// so the difference across the end (a flux slot of Sec. 4.3 that does not
+// exist) is zero and K takes its one-sided form.
 template <int ACTX>
 __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const double* __restrict__ z,
                                                       double* __restrict__ y, double* __restrict__ ybar,
@@ -125,8 +179,12 @@ __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const dou
   constexpr int NW = ACTX ? 4 : 2;
   const long long n = g.n;
   const double tau = sc->tau;
-  const double inv_tau = 1.0 / tau;
+  const ProxK K = prox_consts(tau, cf.f_b);
   const double theta = 1.0 / sqrt(1.0 + 2.0 * cf.gamma * tau);
+  const double t_nu = tau * g.nu, t_idt = tau * g.idt, t_idx = tau * g.idx, t_idy = tau * g.idy;
+  const double a1_in = fma(tau, cf.f_a, 1.0), a1_last = fma(tau, fma(cf.g_a, g.idt, cf.f_a), 1.0);
+  const float a1f_in = (float)a1_in, a1f_last = (float)a1_last;
+  const df a1d_in = df_from_double(a1_in), a1d_last = df_from_double(a1_last);
   double acc = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
@@ -136,60 +194,45 @@ __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const dou
     const int k = (int)(t / g.nx);
     const long long base = (long long)k * g.S;
     const long long rowi = base + (long long)i * g.ny;
-    // x = C^T z at this cell
+    const int jm = j == 0 ? (g.pery ? g.ny - 1 : 0) : j - 1;
+    const int jp = j == g.ny - 1 ? (g.pery ? 0 : g.ny - 1) : j + 1;
     const double zc = z[e];
-    const bool per_y = g.pery;
-    const bool hmy = per_y || j >= 1, hpy = per_y || j <= g.ny - 2;
-    const int jm = hmy ? (j == 0 ? g.ny - 1 : j - 1) : j;
-    const int jp = hpy ? (j == g.ny - 1 ? 0 : j + 1) : j;
-    const double zjm = z[rowi + jm], zjp = z[rowi + jp];
-    // K z: cK z - ay (zN + zS) - ax (zW + zE) away from Neumann ends (fewer FP64 ops)
-    double Kz;
-    double xw[NW];
+    const double dyp = zc - z[rowi + jp], dym = z[rowi + jm] - zc;
+    double Kz = g.ay * (dyp - dym);
+    double d[NW];
     if (ACTX) {
-      const bool per_x = g.perx;
-      const bool hmx = per_x || i >= 1, hpx = per_x || i <= g.nx - 2;
-      const int im = hmx ? (i == 0 ? g.nx - 1 : i - 1) : i;
-      const int ip = hpx ? (i == g.nx - 1 ? 0 : i + 1) : i;
-      const double zim = z[base + (long long)im * g.ny + j], zip = z[base + (long long)ip * g.ny + j];
-      if (hmx && hpx && hmy && hpy)
-        Kz = fma(2.0 * (g.ax + g.ay), zc, -fma(g.ax, zim + zip, g.ay * (zjm + zjp)));
-      else
-        Kz = g.ay * ((hmy ? zc - zjm : 0.0) + (hpy ? zc - zjp : 0.0)) +
-             g.ax * ((hmx ? zc - zim : 0.0) + (hpx ? zc - zip : 0.0));
-      xw[0] = hpx ? (zc - zip) * g.idx : 0.0;
-      xw[1] = hmx ? (zim - zc) * g.idx : 0.0;
-      xw[2] = hpy ? (zc - zjp) * g.idy : 0.0;
-      xw[3] = hmy ? (zjm - zc) * g.idy : 0.0;
+      const int im = i == 0 ? (g.perx ? g.nx - 1 : 0) : i - 1;
+      const int ip = i == g.nx - 1 ? (g.perx ? 0 : g.nx - 1) : i + 1;
+      const double dxp = zc - z[base + (long long)ip * g.ny + j], dxm = z[base + (long long)im * g.ny + j] - zc;
+      Kz = fma(g.ax, dxp - dxm, Kz);
+      d[0] = dxp; d[1] = dxm; d[2] = dyp; d[3] = dym;
     } else {
-      Kz = g.ay * ((hmy ? zc - zjm : 0.0) + (hpy ? zc - zjp : 0.0));
-      xw[0] = hpy ? (zc - zjp) * g.idy : 0.0;
-      xw[1] = hmy ? (zjm - zc) * g.idy : 0.0;
+      d[0] = dyp; d[1] = dym;
     }
     const double zn = (k + 1 < g.nt) ? z[e + g.S] : 0.0;
-    const double xm = fma(g.nu, Kz, (zc - zn) * g.idt);
-    // prox of y - tau x
+    // primal step y - tau x, x_m = nu K z + (z - z_next)/dt, x_w = d / dx
     const double m_old = y[e];
+    const double mbar = fma(-t_nu, Kz, fma(-t_idt, zc - zn, m_old));
     double w_old[NW], wbar[NW], w_new[NW];
 #pragma unroll
     for (int q = 0; q < NW; ++q) {
       w_old[q] = y[e + (q + 1) * n];
-      wbar[q] = w_old[q] - tau * xw[q];
+      wbar[q] = fma(-((ACTX && q < 2) ? t_idx : t_idy), d[q], w_old[q]);
     }
     const bool last = (k == g.nt - 1);
     const long long f = (long long)i * g.ny + j;
-    const double a = cf.f_a + (last ? cf.g_a * g.idt : 0.0);
-    const double cc = V[f] + (last ? W[f] * g.idt : 0.0);
+    const double cc = last ? fma(W[f], g.idt, V[f]) : V[f];
     double m_new;
-    prox_cell<NW>(m_old - tau * xm, wbar, tau, inv_tau, a, cf.f_b, cc, m_new, w_new);
+    prox_cell<NW>(mbar, wbar, K, last ? a1_last : a1_in, last ? a1f_last : a1f_in, last ? a1d_last : a1d_in, cc,
+                  m_new, w_new);
+    const double dm = m_new - m_old;
     y[e] = m_new;
-    ybar[e] = m_new + theta * (m_new - m_old);
+    ybar[e] = fma(theta, dm, m_new);
 #pragma unroll
     for (int q = 0; q < NW; ++q) {
       y[e + (q + 1) * n] = w_new[q];
-      ybar[e + (q + 1) * n] = w_new[q] + theta * (w_new[q] - w_old[q]);
+      ybar[e + (q + 1) * n] = fma(theta, w_new[q] - w_old[q], w_new[q]);
     }
-    const double dm = m_new - m_old;
     acc = fma(dm, dm, acc);
   }
   double part[1] = {acc};
@@ -226,7 +269,10 @@ __global__ void __launch_bounds__(kThreads) k_prox_plain(Geom g, Coef cf, double
                                                          const double* __restrict__ W) {
   constexpr int NW = ACTX ? 4 : 2;
   const long long n = g.n;
-  const double inv_tau = 1.0 / tau;
+  const ProxK K = prox_consts(tau, cf.f_b);
+  const double a1_in = fma(tau, cf.f_a, 1.0), a1_last = fma(tau, fma(cf.g_a, g.idt, cf.f_a), 1.0);
+  const float a1f_in = (float)a1_in, a1f_last = (float)a1_last;
+  const df a1d_in = df_from_double(a1_in), a1d_last = df_from_double(a1_last);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     const int k = (int)(e / g.S);
@@ -235,10 +281,10 @@ __global__ void __launch_bounds__(kThreads) k_prox_plain(Geom g, Coef cf, double
 #pragma unroll
     for (int q = 0; q < NW; ++q) wbar[q] = v[e + (q + 1) * n];
     const bool last = (k == g.nt - 1);
-    const double a = cf.f_a + (last ? cf.g_a * g.idt : 0.0);
-    const double cc = V[f] + (last ? W[f] * g.idt : 0.0);
+    const double cc = last ? fma(W[f], g.idt, V[f]) : V[f];
     double m_new;
-    prox_cell<NW>(v[e], wbar, tau, inv_tau, a, cf.f_b, cc, m_new, w_new);
+    prox_cell<NW>(v[e], wbar, K, last ? a1_last : a1_in, last ? a1f_last : a1f_in, last ? a1d_last : a1d_in, cc,
+                  m_new, w_new);
     y[e] = m_new;
 #pragma unroll
     for (int q = 0; q < NW; ++q) y[e + (q + 1) * n] = w_new[q];
