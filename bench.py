@@ -134,9 +134,10 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# FP64 flops of one AAt apply per unknown in the fused factored form: K p
-# (4 differences, 2 adds, 2 scalings, 1 add = 9), xm = nu Kp + (p - p')/dt (4),
-# q = nu K xm + (xm - xm')/dt + 2 Kp (10 + 2 + 2) -> 27.
+# Algorithmic FP64 flops of one AAt apply per unknown in the factored form
+# q = C (C^T p): K p (4 differences, 2 adds, 2 scalings, 1 add = 9),
+# xm = nu Kp + (p - p')/dt (4), q = nu K xm + (xm - xm')/dt + 2 Kp (10 + 2 + 2)
+# -> 27.  (The kernels issue 15 FP64 instructions per unknown, mostly FMAs.)
 AAT_FLOPS_PER_UNKNOWN = 27
 # GB300 FP64 rate (recipe table: 1.25 TFLOP/s); an FMA-chain probe on this machine
 # measured 1.196 TFLOP/s.
@@ -364,8 +365,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     err_mixed = float(torch.linalg.norm(y - y64) / torch.linalg.norm(y64))
 
-    # Dominant-kernel roofline: the fused AAt stencil, timed with CUDA events on
-    # the stream it is launched on, same launch shape as inside the solve graph.
+    # Dominant-kernel roofline: the AAt apply (its two stencil passes, k_aat_x and
+    # k_aat_q), timed with CUDA events on the stream it is launched on, same
+    # launch shapes as inside the solve graph.
     p_in = torch.randn(n_per, dtype=torch.float64, device=dev)
     q_out = torch.empty_like(p_in)
     for _ in range(3):
@@ -380,7 +382,7 @@ def run_gpu(args):
     t_aat = a0.elapsed_time(a1) / 1e3 / reps
     flops = AAT_FLOPS_PER_UNKNOWN * n_per
     achieved = flops / t_aat / 1e12
-    traffic = profiled_traffic("k_AAt_config2.md")
+    traffic = profiled_traffic("k_aat_config2.md")
 
     # End to end through the host-buffer entry point (copies inside the timed region).
     pin = lambda a: torch.as_tensor(a).pin_memory()
@@ -434,11 +436,11 @@ def run_gpu(args):
             "fp64_path": {"value": cp64 / t64, "unit": "CP iterations/s", "ms_per_step": 1e3 * t64},
             "mixed_vs_fp64_speedup": (cp_all / t) / (cp64 / t64) / world,
             "mixed_rel_err_vs_fp64_path": err_mixed,
-            "roofline": {"kernel": "k_AAt (fused C C^T stencil, FP64)", "bound": "alu",
+            "roofline": {"kernel": "AAt apply: k_aat_x + k_aat_q (C C^T stencil, FP64)", "bound": "alu",
                          "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                          "algorithmic_flops_per_launch": flops, "avg_launch_us": 1e6 * t_aat,
-                         "hbm_achieved_gbs": 16 * n_per / t_aat / 1e9,
+                         "hbm_achieved_gbs": 56 * n_per / t_aat / 1e9,
                          "hbm_peak_gbs": peaks.get("hbm_gbs"), "peak_source": src},
             "cpu_baseline": cpu,
             "e2e": {"value": cp_e2e / t_e2e, "unit": "CP iterations/s", "h2d_bytes_per_step": h2d,
