@@ -550,7 +550,7 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cp-per-step", type=int, default=CP_PER_STEP)
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_df", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_tc", "mixed_df", "fp64"])
     ap.add_argument("--quick", action="store_true", help="main timed loop only (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and uneven-batch lines")
     ap.add_argument("--kernels-only", action="store_true",

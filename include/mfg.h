@@ -57,8 +57,12 @@ enum { MFG_PERIODIC = 0, MFG_NEUMANN = 1 };
  * dot products and the prox stay FP64.  MFG_MIXED_DF: as MFG_MIXED, with the
  * AAt stencil evaluated in double-float arithmetic (pairs of FP32 numbers,
  * ~48 significant bits) from FP64 inputs to FP64 outputs; residuals, dot
- * products and the prox stay FP64.  GB300 issues FP32 at ~58x its FP64 rate. */
-enum { MFG_FP64 = 0, MFG_MIXED = 1, MFG_MIXED_DF = 2 };
+ * products and the prox stay FP64.  MFG_MIXED_TC: as MFG_MIXED, with the
+ * preconditioner's dense time transforms (DCT-VIII / DST-I products, Sec. 4.2)
+ * on the tensor cores (tcgen05, TF32 operands split in three products for
+ * ~FP32 accuracy) when N_t is 32, 64 or 128, on the CUDA cores otherwise.
+ * GB300 issues FP32 at ~58x its FP64 rate. */
+enum { MFG_FP64 = 0, MFG_MIXED = 1, MFG_MIXED_DF = 2, MFG_MIXED_TC = 3 };
 /* PCG tolerance: fixed cg_tol, or the paper's rule
  * min{1e-4, max{1e-6, 1e-4 r}} with r the last CP step (Sec. 5). */
 enum { MFG_CG_FIXED = 0, MFG_CG_ADAPTIVE = 1 };
@@ -86,7 +90,7 @@ typedef struct {
   int cg_rule;       /* MFG_CG_FIXED | MFG_CG_ADAPTIVE                                 */
   double cg_tol;     /* relative PCG tolerance for MFG_CG_FIXED                        */
   int max_cg;        /* PCG iteration cap per solve                                    */
-  int precision;     /* MFG_FP64 | MFG_MIXED | MFG_MIXED_DF                            */
+  int precision;     /* MFG_FP64 | MFG_MIXED | MFG_MIXED_DF | MFG_MIXED_TC             */
 } mfg_problem;
 
 /* Per-instance run record.  On entry to mfg_solve, `ell`, `tau`, `sigma` are

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libmfg_gb300.so")
 MFG_OK, MFG_ERR_INVALID_ARG, MFG_ERR_UNSUPPORTED, MFG_ERR_CUDA = 0, 1, 2, 3
 MFG_ERR_NOT_CONVERGED, MFG_ERR_NONFINITE, MFG_ERR_TIMEOUT = 4, 5, 6
 MFG_PERIODIC, MFG_NEUMANN = 0, 1
-MFG_FP64, MFG_MIXED, MFG_MIXED_DF = 0, 1, 2
+MFG_FP64, MFG_MIXED, MFG_MIXED_DF, MFG_MIXED_TC = 0, 1, 2, 3
 MFG_CG_FIXED, MFG_CG_ADAPTIVE = 0, 1
 MFG_LAUNCH_GRAPH, MFG_LAUNCH_EAGER = 0, 1
 
@@ -104,7 +104,8 @@ def problem_struct(d, precision=None):
     p.max_cp, p.cp_tol, p.cg_rule = d["max_cp"], d["cp_tol"], d["cg_rule"]
     p.cg_tol, p.max_cg = d["cg_tol"], d["max_cg"]
     prec = d.get("precision", "fp64") if precision is None else precision
-    p.precision = {"fp64": MFG_FP64, "mixed": MFG_MIXED, "mixed_df": MFG_MIXED_DF}.get(prec, prec)
+    p.precision = {"fp64": MFG_FP64, "mixed": MFG_MIXED, "mixed_df": MFG_MIXED_DF,
+                   "mixed_tc": MFG_MIXED_TC}.get(prec, prec)
     return p
 
 

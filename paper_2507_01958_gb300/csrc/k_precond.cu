@@ -572,7 +572,7 @@ static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, c
                           const T* dcty, const T* thc, const T* thd, const T* tho,
                           const double* r, double* z, T* w0, T* w1,
                           const DevScalars* sc, cudaStream_t s, const PcgDot* dot,
-                          const PcgZr* zr) {
+                          const PcgZr* zr, bool tc = false) {
   const long long S = g.S, n = g.n;
   const bool fy = twy != nullptr && fft_supported(g.ny);
   const bool fx = twx != nullptr && fft_supported(g.nx);
@@ -592,10 +592,16 @@ static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, c
       axis_pass<T, T, T>(a, b, Hx, g.nx, g.ny, (long long)g.nt, 0, sc, s);
     T* t = a; a = b; b = t;
   }
-  if (thc != nullptr)
+  if (thc != nullptr) {
     k_thomas<T><<<(int)((S + 255) / 256), 256, 0, s>>>(a, b, thc, thd, tho, g.nt, (int)S, sc);
-  else
+  } else if constexpr (sizeof(T) == 4) {
+    if (tc && time_tc_supported(g.nt))
+      launch_time_tc(a, b, V, lamt, L1, L2, g.nt, (int)S, sc, s);
+    else
+      time_pass<T>(a, b, V, lamt, L1, L2, g.nt, (int)S, sc, s);
+  } else {
     time_pass<T>(a, b, V, lamt, L1, L2, g.nt, (int)S, sc, s);
+  }
   { T* t = a; a = b; b = t; }
   if (g.nx > 1) {
     if (fx)
@@ -615,10 +621,10 @@ static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, c
 void launch_precond(const Geom& g, const PrecTables& t, int precision, const double* r, double* z,
                     double* work64, float* work32, const DevScalars* sc, cudaStream_t s,
                     const PcgDot* dot, const PcgZr* zr) {
-  if (precision == MFG_MIXED || precision == MFG_MIXED_DF)
+  if (precision == MFG_MIXED || precision == MFG_MIXED_DF || precision == MFG_MIXED_TC)
     precond_typed<float>(g, t.Hx32, t.Hy32, t.Vt32, t.lamt32, t.L1_32, t.L2_32, t.twx32, t.dctx32,
                          t.twy32, t.dcty32, t.thc32, t.thd32, t.tho32, r, z, work32, work32 + g.n,
-                         sc, s, dot, zr);
+                         sc, s, dot, zr, precision == MFG_MIXED_TC);
   else
     precond_typed<double>(g, t.Hx64, t.Hy64, t.Vt64, t.lamt64, t.L1_64, t.L2_64, t.twx64, t.dctx64,
                           t.twy64, t.dcty64, t.thc64, t.thd64, t.tho64, r, z, work64, work64 + g.n,
@@ -648,6 +654,7 @@ int precond_configure() {
   MFG_TF_ATTR(double, 32) MFG_TF_ATTR(double, 64) MFG_TF_ATTR(double, 128)
 #undef MFG_TF_ATTR
   bad |= fft_configure() != MFG_OK;
+  bad |= time_tc_configure() != MFG_OK;
   return bad ? MFG_ERR_CUDA : MFG_OK;
 }
 

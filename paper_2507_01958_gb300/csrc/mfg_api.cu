@@ -85,8 +85,10 @@ int validate_problem(const mfg_problem& p, int idx) {
     return set_error(MFG_ERR_INVALID_ARG, "cg_rule must be MFG_CG_FIXED or MFG_CG_ADAPTIVE" + at);
   if (p.cg_rule == MFG_CG_FIXED && !(p.cg_tol > 0.0))
     return set_error(MFG_ERR_INVALID_ARG, "cg_tol must be > 0" + at);
-  if (p.precision != MFG_FP64 && p.precision != MFG_MIXED && p.precision != MFG_MIXED_DF)
-    return set_error(MFG_ERR_INVALID_ARG, "precision must be MFG_FP64, MFG_MIXED or MFG_MIXED_DF" + at);
+  if (p.precision != MFG_FP64 && p.precision != MFG_MIXED && p.precision != MFG_MIXED_DF &&
+      p.precision != MFG_MIXED_TC)
+    return set_error(MFG_ERR_INVALID_ARG,
+                     "precision must be MFG_FP64, MFG_MIXED, MFG_MIXED_DF or MFG_MIXED_TC" + at);
   const double nxy = (double)p.n[0] * (p.dim == 2 ? p.n[1] : 1);
   if (nxy * p.nt > 4.0e9) return set_error(MFG_ERR_INVALID_ARG, "instance too large" + at);
   return MFG_OK;

@@ -107,6 +107,11 @@ struct PrecTables {
   double *thc64 = nullptr, *thd64 = nullptr, *tho64 = nullptr;
   float *thc32 = nullptr, *thd32 = nullptr, *tho32 = nullptr;
 };
+// Tensor-core time pass (MFG_MIXED_TC), for N_t in {32, 64, 128}.
+bool time_tc_supported(int nt);
+void launch_time_tc(const float* in, float* out, const float* V, const float* lamt, const float* L1,
+                    const float* L2, int nt, int S, const DevScalars* sc, cudaStream_t s);
+int time_tc_configure();
 int build_prec_tables(const mfg_problem& p, const Geom& g, PrecTables* t, std::string* err);
 void free_prec_tables(PrecTables* t);
 // Operands of the PCG dot products that the last preconditioner pass can fuse
