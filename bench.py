@@ -10,7 +10,10 @@ One step = one fixed-count solve: 300 accelerated Chambolle-Pock iterations
 per-cell prox) on each of the four instances, started from the initial
 iterate; the four instances run as parallel branches of one CUDA graph launch.
 Metric: CP iterations per second, summed over instances (each CP iteration is
-one preconditioned AAt solve).
+one preconditioned AAt solve).  Precision (default): the preconditioner in
+FP32 with its dense time transforms on the tensor cores (tcgen05, split TF32),
+inside FP64 flexible PCG with an FP64 AAt, FP64 residuals and dot products;
+--precision mixed keeps the time transforms on the CUDA cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -138,6 +141,9 @@ def load_peaks():
 # q = C (C^T p): K p (4 differences, 2 adds, 2 scalings, 1 add = 9),
 # xm = nu Kp + (p - p')/dt (4), q = nu K xm + (xm - xm')/dt + 2 Kp (10 + 2 + 2)
 # -> 27.  (The kernels issue 15 FP64 instructions per unknown, mostly FMAs.)
+# Precision of the timed solve and of the extras: FP32 preconditioner with the
+# time transforms on the tensor cores (tcgen05, split TF32), FP64 elsewhere.
+PRECISION = "mixed_tc"
 AAT_FLOPS_PER_UNKNOWN = 27
 # GB300 FP64 rate (recipe table: 1.25 TFLOP/s); an FMA-chain probe on this machine
 # measured 1.196 TFLOP/s.
@@ -162,7 +168,7 @@ def adjoint_measure(dev, cp_iters=300):
     import paper_2507_01958_gb300 as pkg
     L = pkg.lib()
     inst = mi.config4()
-    p = dict(inst["problem"], max_cp=cp_iters, cg_tol=CG_TOL, precision="mixed")
+    p = dict(inst["problem"], max_cp=cp_iters, cg_tol=CG_TOL, precision=PRECISION)
     plan = L.mfg_plan(p)
     n = p["nt"] * p["n"][0] * p["n"][1]
     S = p["n"][0] * p["n"][1]
@@ -216,6 +222,77 @@ def exact_time_measure(dev, L, insts, m0, V, W, y0, stream, cp_iters=CP_PER_STEP
             "unit": "CP iterations/s", "avg_pcg_per_cp": cg / max(cp, 1), "ms_per_step": 1e3 * t}
 
 
+def config3_measure(dev, peak_gbs, cp_iters=3):
+    """The 2-D Neumann 512^2 x 128 workload (n = 33,554,432): each hot entry
+    point timed with CUDA events (achieved bandwidth = the kernels' own
+    read + write bytes per call / time, against the HBM peak), and a short
+    mixed-precision CP solve from the initial iterate."""
+    import torch
+    import paper_2507_01958_gb300 as pkg
+    L = pkg.lib()
+    inst = mi.config3()
+    p0 = inst["problem"]
+    n = p0["nt"] * p0["n"][0] * p0["n"][1]
+    todev = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).reshape(-1).to(dev)
+    V, W, m0 = todev(inst["V"]), todev(inst["W"]), todev(inst["m0"])
+    g = torch.Generator(device=dev).manual_seed(3)
+    r = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+    z = torch.empty_like(r)
+    v = torch.randn(5 * n, dtype=torch.float64, device=dev, generator=g)
+    v[:n] += 2.0
+    yv = torch.empty_like(v)
+
+    def timed(f, reps=5):
+        for _ in range(2):
+            f()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            f()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3 / reps
+
+    def entry(t, nbytes, bound):
+        return {"us": 1e6 * t, "bytes_per_call": nbytes, "achieved_gbs": nbytes / t / 1e9,
+                "hbm_frac": nbytes / t / 1e9 / peak_gbs, "bound": bound}
+
+    out = {"workload": "2-D Neumann 512^2 x N_t 128, nu = 1e-2 (n = 33,554,432)"}
+    kern = {}
+    plan = L.mfg_plan(dict(p0, precision="mixed"))
+    kern["AAt apply (k_aat_x + k_aat_q)"] = entry(timed(lambda: L.mfg_apply_AAt(plan, 0, r, z)), 16 * n,
+                                                   "FP64 issue")
+    kern["C apply (k_apply_C)"] = entry(timed(lambda: L.mfg_apply_C(plan, 0, v, z)), 48 * n, "FP64 issue")
+    kern["prox (k_prox_plain)"] = entry(timed(lambda: L.mfg_prox(plan, 0, 0.5, v, V, W, yv)), 80 * n,
+                                        "FP64 issue")
+    # five passes: FP64 -> FP32, three FP32 -> FP32, FP32 -> FP64
+    kern["P^-1 apply, FP32 (5 passes)"] = entry(timed(lambda: L.mfg_apply_precond(plan, 0, r, z)), 48 * n,
+                                                 "HBM / latency")
+    plan_tc = L.mfg_plan(dict(p0, precision="mixed_tc"))
+    kern["P^-1 apply, tensor-core time pass"] = entry(timed(lambda: L.mfg_apply_precond(plan_tc, 0, r, z)),
+                                                       48 * n, "HBM / latency")
+    out["kernels"] = kern
+    del v, yv
+    # short CP solve, mixed precision, from the initial iterate
+    y0 = todev(inst["y0"])
+    y, ybar, zz = y0.clone(), y0.clone(), torch.zeros(n, dtype=torch.float64, device=dev)
+    ps = L.mfg_plan(dict(p0, precision=PRECISION, max_cp=cp_iters, cg_tol=CG_TOL))
+    L.mfg_solve(ps, m0, V, W, y, ybar, zz)  # builds the graph
+    y.copy_(y0); ybar.copy_(y0); zz.zero_()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    rc, st = L.mfg_solve(ps, m0, V, W, y, ybar, zz)
+    b.record()
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    out["cp"] = {"cp_iters": st[0].cp_iters, "value": st[0].cp_iters / t, "unit": "CP iterations/s",
+                 "avg_pcg_per_cp": st[0].cg_iters / max(st[0].cp_iters, 1),
+                 "note": f"the first {cp_iters} CP iterations from the initial iterate, precision {PRECISION}"}
+    return out
+
+
 def batch_measure(dev, count=64, cp_iters=20):  # noqa: C901
     """The uneven batch: `count` seeded instances (periodic or Neumann, N in
     {64,128,256}, N_t in {32,64,128}, nu log-uniform) in one plan and one graph
@@ -224,7 +301,7 @@ def batch_measure(dev, count=64, cp_iters=20):  # noqa: C901
     import paper_2507_01958_gb300 as pkg
     L = pkg.lib()
     insts = mi.config5(count=count, with_y0=False)
-    probs = [dict(i["problem"], max_cp=cp_iters, cg_tol=CG_TOL, precision="mixed") for i in insts]
+    probs = [dict(i["problem"], max_cp=cp_iters, cg_tol=CG_TOL, precision=PRECISION) for i in insts]
     plan = L.mfg_plan(probs)
     sz = L.mfg_sizes(plan)
 
@@ -406,6 +483,7 @@ def run_gpu(args):
     exact = exact_time_measure(dev, L, insts, m0, V, W, y0, stream) if not args.no_extras else None
     adj = adjoint_measure(dev) if not args.no_extras else None
     batch = batch_measure(dev) if not args.no_extras else None
+    big = config3_measure(dev, load_peaks()[0].get("hbm_gbs", 6800.0)) if not args.no_extras else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -428,7 +506,7 @@ def run_gpu(args):
             "data": "synthetic (seeded fields shaped like the paper's experiments)",
             "config": {"workload": WORKLOAD, "instances": len(NUS), "unknowns_per_instance": n_per,
                        "primal_unknowns_per_instance": 5 * n_per, "pcg_rel_tol": CG_TOL,
-                       "precision": "mixed", "parallelism": f"replicas x{world}",
+                       "precision": args.precision, "parallelism": f"replicas x{world}",
                        "l2": "working set 4 x ~128 MB > 129 MB L2; no flush"},
             "pcg_iters_per_s": cg_all / t,
             "unknowns_cp_iters_per_s": cp_all * n_per / t,
@@ -450,6 +528,7 @@ def run_gpu(args):
             "exact_time_solve": exact,
             "adjoint": adj,
             "batch_uneven": batch,
+            "config3": big,
         }
         print(json.dumps(out))
     if world > 1:
@@ -550,7 +629,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cp-per-step", type=int, default=CP_PER_STEP)
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_tc", "mixed_df", "fp64"])
+    ap.add_argument("--precision", default=PRECISION, choices=["mixed", "mixed_tc", "mixed_df", "fp64"],
+                    help="precision of the timed solve (default: FP32 preconditioner with the tensor-core time pass)")
     ap.add_argument("--quick", action="store_true", help="main timed loop only (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the adjoint and uneven-batch lines")
     ap.add_argument("--kernels-only", action="store_true",

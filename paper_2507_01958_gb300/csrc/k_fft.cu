@@ -82,33 +82,65 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
   const long long line0 = (long long)blockIdx.x * LB;
   const long long o = blockIdx.y;
 
-  // ---- load LB real lines (with the fused z, r update when ZR)
-  double rr = 0.0;
-  double alpha = 0.0;
-  if constexpr (ZR) alpha = zf.sc->alpha;
-  for (int idx = tid; idx < LB * N; idx += 256) {
-    int l, i;
+  // ---- load LB real lines (with the fused z, r update when ZR).  A thread
+  // takes its elements in batches whose loads are all issued before any of
+  // them is used or stored, so one memory latency covers a batch.
+  constexpr int PER = (LB * N + 255) / 256;        // elements per thread
+  constexpr int BL = ZR ? (PER < 4 ? PER : 4) : (PER < 8 ? PER : 8);
+  auto element = [&](int idx, int& l, int& i, long long& addr) -> bool {
     if (CONTIG) { l = idx / N; i = idx % N; } else { i = idx / LB; l = idx % LB; }
     const long long line = line0 + l;
-    T v = T(0);
-    if (line < nlines) {
-      const long long addr = CONTIG ? line * N + i : (o * N + i) * inner + line;
-      if constexpr (ZR) {
-        zf.z[addr] = fma(alpha, zf.p[addr], zf.z[addr]);
-        const double rv = fma(-alpha, zf.q[addr], zf.r[addr]);
-        zf.r[addr] = rv;
-        rr = fma(rv, rv, rr);
-        v = (T)rv;
-      } else {
-        v = (T)in[addr];
-      }
-    }
+    addr = CONTIG ? line * N + i : (o * N + i) * inner + line;
+    return idx < LB * N && line < nlines;
+  };
+  auto stage = [&](int l, int i, T v) {
     if (MODE == FFT_DCT3) {
       real1[l * NP + i] = v;
     } else {
       const int p = (MODE == FFT_DCT2) ? ((i & 1) ? N - 1 - (i >> 1) : (i >> 1)) : i;
       T* dst = reinterpret_cast<T*>(&buf0[(l >> 1) * NP + p]);
       dst[l & 1] = v;
+    }
+  };
+  double rr = 0.0;
+  const double alpha = ZR ? zf.sc->alpha : 0.0;
+#pragma unroll 1
+  for (int b0 = 0; b0 < PER; b0 += BL) {
+    int ls[BL], is[BL];
+    long long ad[BL];
+    bool lv[BL];
+#pragma unroll
+    for (int u = 0; u < BL; ++u) {
+      const int idx = tid + 256 * (b0 + u);
+      lv[u] = (b0 + u < PER) && element(idx, ls[u], is[u], ad[u]);
+      if (!(idx < LB * N)) ls[u] = -1;
+    }
+    if constexpr (ZR) {
+      double zv[BL], pv[BL], rv[BL], qv[BL];
+#pragma unroll
+      for (int u = 0; u < BL; ++u) {
+        zv[u] = lv[u] ? zf.z[ad[u]] : 0.0;
+        pv[u] = lv[u] ? zf.p[ad[u]] : 0.0;
+        rv[u] = lv[u] ? zf.r[ad[u]] : 0.0;
+        qv[u] = lv[u] ? zf.q[ad[u]] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < BL; ++u) {
+        const double rn = fma(-alpha, qv[u], rv[u]);
+        if (lv[u]) {
+          zf.z[ad[u]] = fma(alpha, pv[u], zv[u]);
+          zf.r[ad[u]] = rn;
+        }
+        rr = fma(rn, rn, rr);
+        if (ls[u] >= 0) stage(ls[u], is[u], (T)rn);
+      }
+    } else {
+      T v[BL];
+#pragma unroll
+      for (int u = 0; u < BL; ++u) v[u] = lv[u] ? (T)in[ad[u]] : T(0);
+#pragma unroll
+      for (int u = 0; u < BL; ++u)
+        if (ls[u] >= 0) stage(ls[u], is[u], v[u]);
     }
   }
   __syncthreads();
@@ -185,19 +217,37 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
   }
   __syncthreads();
 
-  // ---- store (with the fused dot products of the PCG step when DOT)
+  // ---- store (with the fused dot products of the PCG step when DOT; a
+  // batch's dot operands are loaded before its stores)
   double a0 = 0.0, a1 = 0.0;
-  for (int idx = tid; idx < LB * N; idx += 256) {
-    int l, i;
-    if (CONTIG) { l = idx / N; i = idx % N; } else { i = idx / LB; l = idx % LB; }
-    const long long line = line0 + l;
-    if (line < nlines) {
-      const long long addr = CONTIG ? line * N + i : (o * N + i) * inner + line;
-      const TO v = (TO)R[l * NP + i];
-      out[addr] = v;
-      if constexpr (DOT) {
-        a0 = fma(df.r[addr], (double)v, a0);
-        if (df.flex) a1 = fma(df.q[addr], (double)v, a1);
+  constexpr int BS = PER < 8 ? PER : 8;
+#pragma unroll 1
+  for (int b0 = 0; b0 < PER; b0 += BS) {
+    int ls[BS], is[BS];
+    long long ad[BS];
+    bool lv[BS];
+#pragma unroll
+    for (int u = 0; u < BS; ++u) {
+      const int idx = tid + 256 * (b0 + u);
+      lv[u] = (b0 + u < PER) && element(idx, ls[u], is[u], ad[u]);
+    }
+    double dr[DOT ? BS : 1], dq[DOT ? BS : 1];
+    if constexpr (DOT) {
+#pragma unroll
+      for (int u = 0; u < BS; ++u) {
+        dr[u] = lv[u] ? df.r[ad[u]] : 0.0;
+        dq[u] = (lv[u] && df.flex) ? df.q[ad[u]] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < BS; ++u) {
+      if (lv[u]) {
+        const TO v = (TO)R[ls[u] * NP + is[u]];
+        out[ad[u]] = v;
+        if constexpr (DOT) {
+          a0 = fma(dr[u], (double)v, a0);
+          a1 = fma(dq[u], (double)v, a1);
+        }
       }
     }
   }

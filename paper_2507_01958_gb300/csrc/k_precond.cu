@@ -456,10 +456,17 @@ __global__ void __launch_bounds__(256) k_time_fast(const T* __restrict__ in, T* 
   for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x) {
     const int s0 = strip * TW;
     __syncthreads();  // previous strip done with X (and V loaded on the first pass)
-    for (int q = tid; q < NT * TW; q += 256) {
+    // the strip's loads are all issued before the shared-memory stores
+    constexpr int IT = NT * TW / 256;
+    T xl[IT];
+#pragma unroll
+    for (int u = 0; u < IT; ++u) {
+      const int q = tid + 256 * u;
       const int k = q / TW, c = q % TW;
-      X[q] = (s0 + c < S) ? in[(long long)k * S + s0 + c] : T(0);
+      xl[u] = (s0 + c < S) ? in[(long long)k * S + s0 + c] : T(0);
     }
+#pragma unroll
+    for (int u = 0; u < IT; ++u) X[tid + 256 * u] = xl[u];
     __syncthreads();
     T acc[RM][RN];
 #pragma unroll

@@ -10,8 +10,6 @@
 // entries past the ends; on a periodic axis indices wrap.  Both cases use one
 // rule: a point has a "minus" neighbour (hm) and a "plus" neighbour (hp) unless
 // it sits at the matching end of a Neumann axis.
-#include <algorithm>
-
 #include "df64.cuh"
 #include "mfg_internal.cuh"
 #include "reduce.cuh"
@@ -67,6 +65,10 @@ __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __re
   const double* wx2 = v + 2 * n;
   const double* wy1 = ACTX ? v + 3 * n : v + n;
   const double* wy2 = ACTX ? v + 4 * n : v + 2 * n;
+  // alpha folded into the coefficients: r = alpha nu K m + alpha div_h w + alpha (m^k - m^{k-1})/dt
+  const double anu = alpha * g.nu, ax = ACTX ? g.ax : 0.0;
+  const double kc = anu * 2.0 * (ax + g.ay), kx = anu * ax, ky = anu * g.ay;
+  const double aix = alpha * g.idx, aiy = alpha * g.idy, aidt = alpha * g.idt;
   double acc = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
@@ -75,25 +77,29 @@ __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __re
     const int i = (int)(t % g.nx);
     const int k = (int)(t / g.nx);
     const long long base = (long long)k * g.S;
-    const Nb by = nbr(j, g.ny, g.pery);
     const long long rowi = base + (long long)i * g.ny;
+    // K m with the point itself as the missing neighbour at a Neumann end (one-sided rows)
+    const Nb by = nbr(j, g.ny, g.pery);
     const double mc = m[e];
-    double Km = g.ay * ((by.hm ? mc - m[rowi + by.im] : 0.0) + (by.hp ? mc - m[rowi + by.ip] : 0.0));
-    double bw = g.idy * ((by.hp ? wy1[e] : 0.0) - (by.hm ? wy1[rowi + by.im] : 0.0) +
-                         (by.hp ? wy2[rowi + by.ip] : 0.0) - (by.hm ? wy2[e] : 0.0));
+    double t1 = ky * (m[rowi + by.im] + m[rowi + by.ip]);
+    // div_h w: flux slots past a Neumann end do not exist and read as zero
+    const double sy = ((by.hp ? wy1[e] : 0.0) - (by.hm ? wy1[rowi + by.im] : 0.0)) +
+                      ((by.hp ? wy2[rowi + by.ip] : 0.0) - (by.hm ? wy2[e] : 0.0));
+    double val;
     if (ACTX) {
       const Nb bx = nbr(i, g.nx, g.perx);
       const long long em = base + (long long)bx.im * g.ny + j, ep = base + (long long)bx.ip * g.ny + j;
-      Km += g.ax * ((bx.hm ? mc - m[em] : 0.0) + (bx.hp ? mc - m[ep] : 0.0));
-      bw += g.idx * ((bx.hp ? wx1[e] : 0.0) - (bx.hm ? wx1[em] : 0.0) + (bx.hp ? wx2[ep] : 0.0) -
-                     (bx.hm ? wx2[e] : 0.0));
+      t1 = fma(kx, m[em] + m[ep], t1);
+      const double sx = ((bx.hp ? wx1[e] : 0.0) - (bx.hm ? wx1[em] : 0.0)) +
+                        ((bx.hp ? wx2[ep] : 0.0) - (bx.hm ? wx2[e] : 0.0));
+      val = fma(aix, sx, fma(aiy, sy, fma(kc, mc, -t1)));
+    } else {
+      val = fma(aiy, sy, fma(kc, mc, -t1));
     }
-    double val = g.nu * Km + mc * g.idt + bw;
-    if (k >= 1) val -= m[e - g.S] * g.idt;
-    if (m0 != nullptr && k == 0) val -= m0[(long long)i * g.ny + j] * g.idt;
-    val *= alpha;
+    const double mprev = k >= 1 ? m[e - g.S] : (m0 != nullptr ? m0[(long long)i * g.ny + j] : 0.0);
+    val = fma(aidt, mc - mprev, val);
     r[e] = val;
-    acc += (mode == 2) ? pdot[e] * val : val * val;
+    acc = (mode == 2) ? fma(pdot[e], val, acc) : fma(val, val, acc);
   }
   if (mode == 0) return;
   double part[1] = {acc};
@@ -318,148 +324,76 @@ __global__ void __launch_bounds__(AJ * AI) k_aat_q(Geom g, AatCoef a, int kc, co
   }
 }
 
-// Fused one-pass stencil on shared-memory tiles, used by the double-float
-// variant: a block owns a TI x TJ spatial tile and marches over a chunk of
-// planes; p planes are staged with a 2-point halo, xm with a 1-point halo (on
-// a Neumann axis the halos hold mirror images; xm halo slots outside the
-// domain are refreshed from their mirrors after xm is formed).
-constexpr int TI = 16, TJ = 32;
-constexpr int H2I = TI + 4, H2J = TJ + 4;  // p tile with halo 2
-constexpr int H1I = TI + 2, H1J = TJ + 2;  // xm tile with halo 1
-
-int aat_chunk(const Geom& g) {
-  const long long tiles = (long long)((g.ny + TJ - 1) / TJ) * ((g.nx + TI - 1) / TI);
-  long long want = 152 * 4;
-  long long chunks = (want + tiles - 1) / tiles;
-  if (chunks < 1) chunks = 1;
-  if (chunks > g.nt) chunks = g.nt;
-  int kc = (int)((g.nt + chunks - 1) / chunks);
-  if (kc < 2) kc = 2;
-  if (kc > g.nt) kc = g.nt;
-  return kc;
-}
-
 int aat_blocks(const Geom& g) {
-  const int kc = aat_chunk(g);
-  const long long one = (long long)((g.ny + TJ - 1) / TJ) * ((g.nx + TI - 1) / TI) * ((g.nt + kc - 1) / kc);
   const dim3 g2 = aat2_grid(g, aat2_chunk(g));
-  const long long two = (long long)g2.x * g2.y * g2.z;
-  return (int)std::max(one, two);
+  return (int)((long long)g2.x * g2.y * g2.z);
 }
 
-// Index of grid point i on an axis: wrapped when periodic, mirrored across the
-// end when Neumann (i = -1 -> 0, -2 -> 1, N -> N-1, N+1 -> N-2).
-__device__ __forceinline__ int halo_index(int i, int N, int per) {
-  if (i >= 0 && i < N) return i;
-  if (per) {
-    i %= N;
-    return i < 0 ? i + N : i;
-  }
-  int m = i < 0 ? -1 - i : 2 * N - 1 - i;
-  return m < 0 ? 0 : (m >= N ? N - 1 : m);
-}
+// The same two passes in double-float arithmetic (df64.cuh, the MFG_MIXED_DF
+// precision): p is split into FP32 pairs as it is loaded, every stencil
+// operation runs on FP32 pairs, X and Kp are stored as pairs (8 bytes, like a
+// double), and q is joined back to FP64 (one FP64 add) together with the FP64
+// p.q.  About 48 significant bits; ~2 FP64 instructions per point instead of
+// 15, the rest on the FP32 pipes.
+__device__ __forceinline__ df df_scale2(df a) { return df{2.0f * a.hi, 2.0f * a.lo}; }
 
-// The double-float version (df64.cuh): p is split into FP32 pairs as it is
-// staged, every stencil operation runs on FP32 pairs, and q is rebuilt in FP64
-// (one FP64 add per point) together with the FP64 p.q.
-// About 48 significant bits; used by the MFG_MIXED_DF precision.
-__device__ __forceinline__ void load_plane_h2_df(const Geom& g, const double* __restrict__ p, int k,
-                                                 int i0, int j0, df (*dst)[H2J]) {
-  const int tid = threadIdx.x + TJ * threadIdx.y;
-  if (k >= g.nt) {
-    for (int s = tid; s < H2I * H2J; s += TI * TJ) dst[s / H2J][s % H2J] = df{0.0f, 0.0f};
-    return;
+template <int ACTX>
+__global__ void __launch_bounds__(AJ * AI) k_aat_x_df(Geom g, AatCoef ad, int kc, const double* __restrict__ p,
+                                                      df* __restrict__ X, df* __restrict__ KP,
+                                                      const DevScalars* sc, int mode) {
+  if (mode == 1 && sc->cg_done) return;
+  const int j = blockIdx.x * AJ + threadIdx.x, i = blockIdx.y * AI + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  const df ax = df_from_double(ad.ax), ay = df_from_double(ad.ay), cK = df_from_double(ad.cK),
+           ndt = df_from_double(ad.ndt);
+  const int k0 = blockIdx.z * kc, k1 = min(g.nt, k0 + kc);
+  const Cols nb = aat_cols(g, i, j);
+  const long long row = (long long)i * g.ny;
+  long long base = (long long)k0 * g.S;
+  df c = df_from_double(p[base + row + j]);
+  for (int k = k0; k < k1; ++k) {
+    const df pn = (k + 1 < g.nt) ? df_from_double(p[base + g.S + row + j]) : df{0.0f, 0.0f};
+    df t = df_mul(ay, df_add(df_from_double(p[base + row + nb.jm]), df_from_double(p[base + row + nb.jp])));
+    if (ACTX)
+      t = df_add(t, df_mul(ax, df_add(df_from_double(p[base + (long long)nb.im * g.ny + j]),
+                                      df_from_double(p[base + (long long)nb.ip * g.ny + j]))));
+    const df kp = df_sub(df_mul(cK, c), t);
+    X[base + row + j] = df_add(df_mul(ndt, kp), df_sub(c, pn));
+    KP[base + row + j] = kp;
+    c = pn;
+    base += g.S;
   }
-  const double* pk = p + (long long)k * g.S;
-  for (int s = tid; s < H2I * H2J; s += TI * TJ) {
-    const int li = s / H2J, lj = s % H2J;
-    const int gi = halo_index(i0 + li - 2, g.nx, g.perx);
-    const int gj = halo_index(j0 + lj - 2, g.ny, g.pery);
-    dst[li][lj] = df_from_double(pk[(long long)gi * g.ny + gj]);
-  }
-}
-
-template <int ACTX, int WID>
-__device__ __forceinline__ df fast_K_df(const df (*A)[WID], int r, int c, df ax, df ay, df cK) {
-  df t = df_mul(ay, df_add(A[r][c - 1], A[r][c + 1]));
-  if (ACTX) t = df_add(t, df_mul(ax, df_add(A[r - 1][c], A[r + 1][c])));
-  return df_sub(df_mul(cK, A[r][c]), t);
 }
 
 template <int ACTX>
-__global__ void __launch_bounds__(TI * TJ, 2) k_AAt_df(Geom g, int kc, const double* __restrict__ p,
-                                                       double* __restrict__ q, double* partials,
-                                                       DevScalars* sc, int mode) {
+__global__ void __launch_bounds__(AJ * AI) k_aat_q_df(Geom g, AatCoef ad, int kc, const df* __restrict__ X,
+                                                      const df* __restrict__ KP, const double* __restrict__ p,
+                                                      double* __restrict__ q, double* partials, DevScalars* sc,
+                                                      int mode) {
   if (mode == 1 && sc->cg_done) return;
-  __shared__ df P[2][H2I][H2J];
-  __shared__ df XM[H1I][H1J];
-  __shared__ df KP[TI][TJ];
-  const int tj = threadIdx.x, ti = threadIdx.y;
-  const int j0 = blockIdx.x * TJ, i0 = blockIdx.y * TI;
-  const int k0 = blockIdx.z * kc;
-  const int k1 = min(g.nt, k0 + kc);
-  const int gi = i0 + ti, gj = j0 + tj;
-  const bool own = gi < g.nx && gj < g.ny;
-  const double axd = ACTX ? g.ax : 0.0, ayd = g.ay, cKd = 2.0 * (axd + ayd);
-  const df ax = df_from_double(axd), ay = df_from_double(ayd), cK = df_from_double(cKd);
-  const df nax = df_from_double(g.nu * axd), nay = df_from_double(g.nu * ayd),
-           ncK = df_from_double(g.nu * cKd);
-  const df nu = df_from_double(g.nu), idt = df_from_double(g.idt), two = df{2.0f, 0.0f};
-  const bool ghost_x = ACTX && !g.perx && (i0 == 0 || i0 + TI >= g.nx);
-  const bool ghost_y = !g.pery && (j0 == 0 || j0 + TJ >= g.ny);
-  const bool ghosts = ghost_x || ghost_y;
-  const int tid = tj + TJ * ti;
-
-  int cur = 0;
-  load_plane_h2_df(g, p, k0, i0, j0, P[cur]);
-  df xprev{0.0f, 0.0f};
-  if (k0 > 0) {
-    load_plane_h2_df(g, p, k0 - 1, i0, j0, P[cur ^ 1]);
-    __syncthreads();
-    if (own)
-      xprev = df_add(fast_K_df<ACTX, H2J>(P[cur ^ 1], ti + 2, tj + 2, nax, nay, ncK),
-                     df_mul(df_sub(P[cur ^ 1][ti + 2][tj + 2], P[cur][ti + 2][tj + 2]), idt));
-    __syncthreads();
-  }
+  const int j = blockIdx.x * AJ + threadIdx.x, i = blockIdx.y * AI + threadIdx.y;
   double acc = 0.0;
-  for (int k = k0; k < k1; ++k) {
-    load_plane_h2_df(g, p, k + 1, i0, j0, P[cur ^ 1]);
-    __syncthreads();
-    const df (*Pk)[H2J] = P[cur];
-    const df (*Pn)[H2J] = P[cur ^ 1];
-    for (int s = tid; s < H1I * H1J; s += TI * TJ) {
-      const int li = s / H1J, lj = s % H1J;
-      const df kp = fast_K_df<ACTX, H2J>(Pk, li + 1, lj + 1, ax, ay, cK);
-      XM[li][lj] = df_add(df_mul(nu, kp), df_mul(df_sub(Pk[li + 1][lj + 1], Pn[li + 1][lj + 1]), idt));
-      if (li >= 1 && li <= TI && lj >= 1 && lj <= TJ) KP[li - 1][lj - 1] = kp;
+  if (i < g.nx && j < g.ny) {
+    const df c1 = df_from_double(ad.c1), c2 = df_from_double(ad.c2), c4 = df_from_double(ad.c4),
+             idt2 = df_from_double(ad.idt2);
+    const int k0 = blockIdx.z * kc, k1 = min(g.nt, k0 + kc);
+    const Cols nb = aat_cols(g, i, j);
+    const long long row = (long long)i * g.ny;
+    long long base = (long long)k0 * g.S;
+    df xprev = k0 > 0 ? X[base - g.S + row + j] : df{0.0f, 0.0f};
+    for (int k = k0; k < k1; ++k) {
+      const df xc = X[base + row + j];
+      df t = df_mul(c1, df_add(X[base + row + nb.jm], X[base + row + nb.jp]));
+      if (ACTX)
+        t = df_add(t, df_mul(c2, df_add(X[base + (long long)nb.im * g.ny + j], X[base + (long long)nb.ip * g.ny + j])));
+      t = df_add(t, df_mul(idt2, xprev));
+      t = df_sub(t, df_scale2(KP[base + row + j]));
+      const double qv = df_to_double(df_sub(df_mul(c4, xc), t));
+      q[base + row + j] = qv;
+      if (mode == 1) acc = fma(qv, p[base + row + j], acc);
+      xprev = xc;
+      base += g.S;
     }
-    __syncthreads();
-    if (ghosts) {
-      for (int s = tid; s < H1I * H1J; s += TI * TJ) {
-        const int li = s / H1J, lj = s % H1J;
-        const int xi = i0 + li - 1, xj = j0 + lj - 1;
-        const bool ox = ghost_x && (xi < 0 || xi >= g.nx);
-        const bool oy = ghost_y && (xj < 0 || xj >= g.ny);
-        if (ox || oy) {
-          const int mi = ox ? (xi < 0 ? li + 1 : li - 1) : li;
-          const int mj = oy ? (xj < 0 ? lj + 1 : lj - 1) : lj;
-          XM[li][lj] = XM[mi][mj];
-        }
-      }
-      __syncthreads();
-    }
-    if (own) {
-      const df c = XM[ti + 1][tj + 1];
-      const df nKxm = fast_K_df<ACTX, H1J>(XM, ti + 1, tj + 1, nax, nay, ncK);
-      const df val = df_add(df_mul(two, KP[ti][tj]), df_add(df_mul(df_sub(c, xprev), idt), nKxm));
-      xprev = c;
-      const long long e = (long long)k * g.S + (long long)gi * g.ny + gj;
-      const double vd = df_to_double(val);
-      q[e] = vd;
-      acc = fma(vd, p[e], acc);
-    }
-    __syncthreads();
-    cur ^= 1;
   }
   if (mode != 1) return;
   double part[1] = {acc};
@@ -482,19 +416,21 @@ __global__ void __launch_bounds__(TI * TJ, 2) k_AAt_df(Geom g, int kc, const dou
 
 void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, double* partials,
                 DevScalars* sc, int mode, cudaStream_t s, int df64) {
-  if (df64) {
-    const int kc = aat_chunk(g);
-    dim3 grid((g.ny + TJ - 1) / TJ, (g.nx + TI - 1) / TI, (g.nt + kc - 1) / kc);
-    dim3 block(TJ, TI);
-    if (g.actx)
-      k_AAt_df<1><<<grid, block, 0, s>>>(g, kc, p, q, partials, sc, mode);
-    else
-      k_AAt_df<0><<<grid, block, 0, s>>>(g, kc, p, q, partials, sc, mode);
-    return;
-  }
   const AatCoef a = aat_coef(g);
   const int kc = aat2_chunk(g);
   const dim3 grid = aat2_grid(g, kc), block(AJ, AI);
+  if (df64) {
+    df* X = reinterpret_cast<df*>(scratch);
+    df* KP = X + g.n;
+    if (g.actx) {
+      k_aat_x_df<1><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
+      k_aat_q_df<1><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
+    } else {
+      k_aat_x_df<0><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
+      k_aat_q_df<0><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
+    }
+    return;
+  }
   double* X = scratch;
   double* KP = scratch + g.n;
   if (g.actx) {
@@ -506,6 +442,6 @@ void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, doub
   }
 }
 
-int aat_kernel_count(int df64) { return df64 ? 1 : 2; }
+int aat_kernel_count(int) { return 2; }
 
 }  // namespace mfg

@@ -222,15 +222,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       // ---- product 1: D1[m][r] = sum_k X[k][s0 + m] V[r][k]
       for (int kc = 0; kc < NKC && !failed; ++kc) {
-        for (int q = tid; q < TW * KC / 4; q += kTcThreads) {
+        // every load of the chunk is issued before the first shared-memory store
+        constexpr int IT = TW * KC / 4 / kTcThreads;
+        static_assert(IT * kTcThreads * 4 == TW * KC, "whole float4 groups per thread");
+        float x[IT][4];
+#pragma unroll
+        for (int u = 0; u < IT; ++u) {
+          const int q = tid + u * kTcThreads;
           const int mm = q % TW, kq = q / TW;  // consecutive threads: consecutive modes
           const int s = s0 + mm;
           const int k0 = kc * KC + 4 * kq;
-          float x[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) x[i] = s < S ? in[(long long)(k0 + i) * S + s] : 0.0f;
+          for (int i = 0; i < 4; ++i) x[u][i] = s < S ? in[(long long)(k0 + i) * S + s] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < IT; ++u) {
+          const int q = tid + u * kTcThreads;
+          const int mm = q % TW, kq = q / TW;
           float4 h, l;
-          split4(x, h, l);
+          split4(x[u], h, l);
           const uint32_t off = kq * LBO_A + (mm >> 3) * 128u + (mm & 7) * 16u;
           *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Ahi) + off) = h;
           *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Alo) + off) = l;
