@@ -108,8 +108,8 @@ typedef struct {
 
 typedef struct mfg_plan_s* mfg_plan_t;
 
-/* Validates `batch` problems, builds the eigenvalue tables (eq. eigs, Alg. 2
- * lines 1-10) and transform matrices on the host in FP64, uploads them and
+/* Validates `batch` problems, builds the eigenvalue tables (eq. eigs, Alg. 2)
+ * and transform matrices on the host in FP64, uploads them and
  * allocates all device workspace on the current device.  Rejects q' != 2
  * (MFG_ERR_UNSUPPORTED), N_t < 2, N < 2, T <= 0, nu < 0, f_a/f_b/g_a < 0,
  * l not in {0,1,2}, N_t > 256 (UNSUPPORTED).  *out is NULL on failure. */
@@ -151,8 +151,8 @@ int mfg_solve_host(mfg_plan_t plan, const double* m0, const double* V,
                    const double* W, double* y, double* ybar, double* z,
                    mfg_stats* st, void* stream);
 
-/* z = P^{-1} r for instance b (Alg. 1 with Alg. 2 in place of line 6, eq.
- * pstrec), in the plan's precision.  With l = 0 the time transform and the
+/* z = P^{-1} r for instance b (Alg. 1 with Alg. 2 for its per-frequency
+ * spatial solves, eq. pstrec), in the plan's precision.  With l = 0 the time transform and the
  * per-frequency division are replaced by an exact tridiagonal solve in time per
  * spatial mode, so P = AAt (eq. largeA) up to rounding.  r, z: n elements;
  * must not alias. */

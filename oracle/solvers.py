@@ -48,7 +48,7 @@ def solve_cg(A, b, tol=1e-12, x0=None, maxiter=100000):
 
 def laplacian_eigs(prob):
     """Eigenvalues kappa_s of K on the (Nx, Ny) mode grid, in the order of the
-    transforms used by `to_modes` (Alg. 2, lines 1-8)."""
+    transforms used by `to_modes` (Alg. 2)."""
     out = []
     dims = 2 if prob["dim"] == 2 else 1
     for ax in range(dims):

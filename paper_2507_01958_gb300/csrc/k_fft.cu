@@ -1,9 +1,9 @@
 // Spatial passes of the preconditioner by FFT, for axis lengths that are powers
-// of two (Alg. 2 lines 12-16: transform along y, then x, divide, invert).
+// of two (Alg. 2: transform along y, then x, divide, invert).
 //
 // One block takes LB real lines of length N (rows of the contiguous y axis, or
 // columns of the x axis), packs them pairwise into CL = LB/2 complex lines
-// z = x_a + i x_b, runs a radix-2 Stockham FFT per complex line in shared
+// z = x_a + i x_b, runs a radix-4/2 Stockham FFT per complex line in shared
 // memory (one warp per line, natural order in and out), and separates the
 // pair with the Hermitian symmetry of real data:
 //   X_a[k] = (Z[k] + conj Z[N-k]) / 2,  X_b[k] = (Z[k] - conj Z[N-k]) / (2i).
@@ -162,34 +162,63 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
     __syncthreads();
   }
 
-  // ---- radix-2 Stockham FFT, one warp per complex line
+  // ---- Stockham FFT, one warp per complex line, natural order in and out:
+  // radix-4 stages (Ns = 1, 4, 16, ...) then one radix-2 stage when log2 N is
+  // odd, in the mixed-radix Stockham formulation of Govindaraju et al.
+  // (SC 2008): stage (R, Ns) reads v_r = src[j + r N/R], twiddles v_r by
+  // exp(sgn 2 pi i r (j mod Ns) / (R Ns)), takes the R-point DFT and writes
+  // dst[(j - j mod Ns) R + j mod Ns + r Ns].
   constexpr T sgn = (MODE == FFT_DCT3) ? T(1) : T(-1);
   const int warp = tid >> 5, lane = tid & 31;
   int log2n = 0;
   for (int t = N; t > 1; t >>= 1) ++log2n;
+  const int n4 = log2n >> 1, n2 = log2n & 1;
+  // exp(sgn 2 pi i m / N) for 0 <= m < N from the half-circle table
+  auto twid = [&](int m) -> cx<T> {
+    const cx<T> t = tws[m & (N / 2 - 1)];
+    const T f = (m & (N / 2)) ? T(-1) : T(1);
+    return cx<T>{f * t.x, f * sgn * t.y};
+  };
+  auto cmul = [](cx<T> a, cx<T> w) { return cx<T>{a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x}; };
   for (int q = warp; q < CL; q += 8) {
     cx<T>* src = buf0 + q * NP;
     cx<T>* dst = buf1 + q * NP;
-    for (int Ns = 1; Ns < N; Ns <<= 1) {
+    int Ns = 1;
+    for (int st = 0; st < n4; ++st, Ns <<= 2) {
+      for (int j = lane; j < N / 4; j += 32) {
+        const int k = j & (Ns - 1);
+        const int m = k * (N / (4 * Ns));
+        const cx<T> a0 = src[j];
+        const cx<T> a1 = cmul(src[j + N / 4], twid(m));
+        const cx<T> a2 = cmul(src[j + N / 2], twid(2 * m));
+        const cx<T> a3 = cmul(src[j + 3 * N / 4], twid(3 * m));
+        const cx<T> s02{a0.x + a2.x, a0.y + a2.y}, d02{a0.x - a2.x, a0.y - a2.y};
+        const cx<T> s13{a1.x + a3.x, a1.y + a3.y}, d13{a1.x - a3.x, a1.y - a3.y};
+        const int d = ((j - k) << 2) + k;
+        dst[d] = cx<T>{s02.x + s13.x, s02.y + s13.y};
+        dst[d + Ns] = cx<T>{d02.x - sgn * d13.y, d02.y + sgn * d13.x};
+        dst[d + 2 * Ns] = cx<T>{s02.x - s13.x, s02.y - s13.y};
+        dst[d + 3 * Ns] = cx<T>{d02.x + sgn * d13.y, d02.y - sgn * d13.x};
+      }
+      __syncwarp();
+      cx<T>* t = src; src = dst; dst = t;
+    }
+    if (n2) {
       for (int j = lane; j < N / 2; j += 32) {
         const int k = j & (Ns - 1);
-        const int m = k * (N / (2 * Ns));
-        const cx<T> tk = tws[m];
-        const T wc = tk.x, ws = sgn * tk.y;
         const cx<T> a = src[j];
-        const cx<T> b0 = src[j + N / 2];
-        const cx<T> b{b0.x * wc - b0.y * ws, b0.x * ws + b0.y * wc};
+        const cx<T> b = cmul(src[j + N / 2], twid(k * (N / (2 * Ns))));
         const int d = ((j - k) << 1) + k;
         dst[d] = cx<T>{a.x + b.x, a.y + b.y};
         dst[d + Ns] = cx<T>{a.x - b.x, a.y - b.y};
       }
       __syncwarp();
-      cx<T>* t = src; src = dst; dst = t;
     }
   }
   __syncthreads();
-  const cx<T>* Z = (log2n & 1) ? buf1 : buf0;
-  T* R = reinterpret_cast<T*>((log2n & 1) ? buf0 : buf1);  // real output staging [LB][NP]
+  const bool odd = ((n4 + n2) & 1) != 0;  // stages taken: the result is in buf1 after an odd count
+  const cx<T>* Z = odd ? buf1 : buf0;
+  T* R = reinterpret_cast<T*>(odd ? buf0 : buf1);  // real output staging [LB][NP]
 
   // ---- separate the packed pairs and finish the transform
   const T rsn = T(1) / sqrt(T(N));

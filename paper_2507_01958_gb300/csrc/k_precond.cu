@@ -8,10 +8,10 @@
 //   space H, G: periodic axis -> discrete Hartley transform, a real orthonormal
 //         eigenbasis of the circulant Laplacian (same eigenvalues
 //         2 - 2cos(2 pi v/N) as the DFT of Alg. 2); Neumann axis -> DCT-II
-//         (eigenvalues 2 - 2cos(pi v/N), Alg. 2 line 5).
+//         (eigenvalues 2 - 2cos(pi v/N), Alg. 2).
 //   Lambda_1 = nu^2 D^2 + 2 D, Lambda_2 = (nu D + 1/dt)/dt (eq. lambda1, lambda2)
-//   with D the tiled spatial eigenvalues of Alg. 2 line 8; the per-frequency
-//   divisor S = Lambda_1 + lambda_k Lambda_2 (Alg. 2 lines 9-10) is formed on
+//   with D the tiled spatial eigenvalues of Alg. 2; the per-frequency
+//   divisor S = Lambda_1 + lambda_k Lambda_2 (Alg. 2) is formed on
 //   the fly, never stored as an n-sized table.
 //
 // Passes over the data (ping-pong work buffers, 10n words in total):
@@ -456,17 +456,10 @@ __global__ void __launch_bounds__(256) k_time_fast(const T* __restrict__ in, T* 
   for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x) {
     const int s0 = strip * TW;
     __syncthreads();  // previous strip done with X (and V loaded on the first pass)
-    // the strip's loads are all issued before the shared-memory stores
-    constexpr int IT = NT * TW / 256;
-    T xl[IT];
-#pragma unroll
-    for (int u = 0; u < IT; ++u) {
-      const int q = tid + 256 * u;
+    for (int q = tid; q < NT * TW; q += 256) {
       const int k = q / TW, c = q % TW;
-      xl[u] = (s0 + c < S) ? in[(long long)k * S + s0 + c] : T(0);
+      X[q] = (s0 + c < S) ? in[(long long)k * S + s0 + c] : T(0);
     }
-#pragma unroll
-    for (int u = 0; u < IT; ++u) X[tid + 256 * u] = xl[u];
     __syncthreads();
     T acc[RM][RN];
 #pragma unroll
