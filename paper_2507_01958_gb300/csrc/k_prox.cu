@@ -68,11 +68,11 @@ struct ProxK {
   bool tau_ok;                          // tau inside the FP32 fast-path range
 };
 
-__device__ __forceinline__ ProxK prox_consts(double tau, double f_b) {
+__device__ __forceinline__ ProxK prox_consts(double tau, double half_itau, double f_b) {
   ProxK k;
   k.tau = tau;
   k.half_tau = 0.5 * tau;
-  k.half_itau = 0.5 / tau;
+  k.half_itau = half_itau;
   k.tb = tau * f_b;
   k.tauf = (float)tau;
   k.tbf = (float)k.tb;
@@ -178,9 +178,8 @@ __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const dou
                                                       int use_handle) {
   constexpr int NW = ACTX ? 4 : 2;
   const long long n = g.n;
-  const double tau = sc->tau;
-  const ProxK K = prox_consts(tau, cf.f_b);
-  const double theta = 1.0 / sqrt(1.0 + 2.0 * cf.gamma * tau);
+  const double tau = sc->tau, theta = sc->theta;
+  const ProxK K = prox_consts(tau, sc->half_itau, cf.f_b);
   const double t_nu = tau * g.nu, t_idt = tau * g.idt, t_idx = tau * g.idx, t_idy = tau * g.idy;
   const double a1_in = fma(tau, cf.f_a, 1.0), a1_last = fma(tau, fma(cf.g_a, g.idt, cf.f_a), 1.0);
   const float a1f_in = (float)a1_in, a1f_last = (float)a1_last;
@@ -244,8 +243,11 @@ __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const dou
     const double r = sqrt(tot[0]);
     sc->dm2 = tot[0];
     sc->r_last = r;
-    sc->tau = theta * tau;
+    const double tau_next = theta * tau;
+    sc->tau = tau_next;
     sc->sigma = sc->sigma / theta;
+    sc->theta = 1.0 / sqrt(1.0 + 2.0 * cf.gamma * tau_next);
+    sc->half_itau = 0.5 / tau_next;
     sc->ell += 1;
     sc->cp_iters += 1;
     sc->cg_total += sc->cg_it;
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) k_prox_plain(Geom g, Coef cf, double
                                                          const double* __restrict__ W) {
   constexpr int NW = ACTX ? 4 : 2;
   const long long n = g.n;
-  const ProxK K = prox_consts(tau, cf.f_b);
+  const ProxK K = prox_consts(tau, 0.5 / tau, cf.f_b);
   const double a1_in = fma(tau, cf.f_a, 1.0), a1_last = fma(tau, fma(cf.g_a, g.idt, cf.f_a), 1.0);
   const float a1f_in = (float)a1_in, a1f_last = (float)a1_last;
   const df a1d_in = df_from_double(a1_in), a1d_last = df_from_double(a1_last);

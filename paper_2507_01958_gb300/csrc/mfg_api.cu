@@ -426,6 +426,8 @@ int mfg_solve(mfg_plan_t pl, const double* m0, const double* V, const double* W,
     const bool fresh = st[b].ell <= 0;
     h.tau = fresh ? in.p.tau0 : st[b].tau;
     h.sigma = fresh ? in.p.sigma0 : st[b].sigma;
+    h.theta = 1.0 / std::sqrt(1.0 + 2.0 * in.p.gamma * h.tau);
+    h.half_itau = 0.5 / h.tau;
     h.ell = fresh ? 0 : st[b].ell;
     h.r_last = fresh ? INFINITY : st[b].r_last;
     h.cp_tol = in.p.cp_tol;

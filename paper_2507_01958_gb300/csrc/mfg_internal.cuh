@@ -41,8 +41,10 @@ struct Coef {
 // reduction kernels.  Keeping it on the device lets a whole solve run as one
 // graph launch with no host round trip.
 struct DevScalars {
-  // Chambolle-Pock
+  // Chambolle-Pock; theta = 1/sqrt(1 + 2 gamma tau) and 1/(2 tau) of the
+  // current step, formed once per iteration for the prox kernel
   double tau, sigma, r_last, dm2;
+  double theta, half_itau;
   double cg_tol;        // relative tolerance of the current solve
   double cp_tol;
   int ell, cp_left, cp_done, status;
