@@ -141,7 +141,9 @@ int mfg_sizes(mfg_plan_t plan, size_t* field_total, size_t* primal_total,
  * The dual x = prox_{sigma psi*}(...) of eq. CC* is never stored: the library
  * keeps z and forms C^T z where needed.  The whole solve is one CUDA graph
  * launch; the call synchronises `stream` and fills `st` before returning.
- * Returns the first non-OK instance status, or MFG_OK. */
+ * Returns the first non-OK instance status, or MFG_OK (MFG_ERR_TIMEOUT: with
+ * MFG_MIXED_TC, a tensor-core completion wait ran out; the instance stops and
+ * its outputs are unspecified). */
 int mfg_solve(mfg_plan_t plan, const double* m0, const double* V, const double* W,
               double* y, double* ybar, double* z, mfg_stats* st, void* stream);
 
