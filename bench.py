@@ -293,6 +293,44 @@ def config3_measure(dev, peak_gbs, cp_iters=3):
     return out
 
 
+def cufft_compare(dev, reps=20):
+    """cuFFT as a timed comparison only: torch.fft's 2-D real FFT forward and
+    inverse over the 64 planes of one 128^2 x 64 instance (FP32, cuFFT), next
+    to one preconditioner apply of this library on the same grid (FP64 in and
+    out, four spatial FFT passes plus the time pass)."""
+    import torch
+    import paper_2507_01958_gb300 as pkg
+    try:
+        L = pkg.lib()
+        inst = mi.config2(nu=1e-2)
+        p = inst["problem"]
+        x = torch.randn(p["nt"], p["n"][0], p["n"][1], dtype=torch.float32, device=dev)
+
+        def timed(f):
+            for _ in range(3):
+                f()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                f()
+            b.record()
+            torch.cuda.synchronize()
+            return 1e3 * a.elapsed_time(b) / reps
+
+        t_fft = timed(lambda: torch.fft.irfft2(torch.fft.rfft2(x), s=tuple(p["n"])))
+        plan = L.mfg_plan(dict(p, precision=PRECISION))
+        r = torch.randn(x.numel(), dtype=torch.float64, device=dev)
+        z = torch.empty_like(r)
+        t_pre = timed(lambda: L.mfg_apply_precond(plan, 0, r, z))
+        return {"workload": "64 planes of 128^2 (one instance)",
+                "cufft_rfft2_irfft2_fp32_us": t_fft, "precond_apply_us": t_pre,
+                "note": "cuFFT: spatial transforms only (FP32 in/out); precond apply: FP64 in/out, "
+                        "spatial forward and inverse passes, time pass and division"}
+    except Exception as e:  # a comparison only: never let it break the benchmark line
+        return {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+
+
 def batch_measure(dev, count=64, cp_iters=20):  # noqa: C901
     """The uneven batch: `count` seeded instances (periodic or Neumann, N in
     {64,128,256}, N_t in {32,64,128}, nu log-uniform) in one plan and one graph
@@ -484,6 +522,7 @@ def run_gpu(args):
     adj = adjoint_measure(dev) if not args.no_extras else None
     batch = batch_measure(dev) if not args.no_extras else None
     big = config3_measure(dev, load_peaks()[0].get("hbm_gbs", 6800.0)) if not args.no_extras else None
+    fftcmp = cufft_compare(dev) if not args.no_extras else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -529,6 +568,7 @@ def run_gpu(args):
             "adjoint": adj,
             "batch_uneven": batch,
             "config3": big,
+            "cufft_comparison": fftcmp,
         }
         print(json.dumps(out))
     if world > 1:
