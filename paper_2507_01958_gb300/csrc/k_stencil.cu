@@ -279,7 +279,8 @@ __global__ void __launch_bounds__(AJ * AI) k_aat_x(Geom g, AatCoef a, int kc, co
 // mode 0: q = AAt p.  mode 1 (PCG step): also reduces p.q and sets
 // alpha = rz/(p.q) in the device scalars.
 template <int ACTX>
-__global__ void __launch_bounds__(AJ * AI) k_aat_q(Geom g, AatCoef a, int kc, const double* __restrict__ X,
+// 2-D: capped at 64 registers (four 256-thread blocks per SM) to hide the load latency
+__global__ void __launch_bounds__(AJ * AI, ACTX ? 4 : 3) k_aat_q(Geom g, AatCoef a, int kc, const double* __restrict__ X,
                                                    const double* __restrict__ KP, const double* __restrict__ p,
                                                    double* __restrict__ q, double* partials, DevScalars* sc,
                                                    int mode) {
