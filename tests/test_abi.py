@@ -63,3 +63,20 @@ def test_plan_rejects_invalid_problems_without_gpu():
             L.mfg_plan(bad)
         assert e.value.code == code
         assert L.mfg_last_error()
+
+
+def test_precision_codes_match_header():
+    """The binding's precision names map to the header's enum values, and an
+    unknown code is rejected on the host."""
+    import mfg_inputs as mi
+    L = _lib()
+    txt = open(HEADER).read()
+    enum = dict((k, int(v)) for k, v in re.findall(r"(MFG_(?:FP64|MIXED(?:_DF|_TC)?))\s*=\s*(\d+)", txt))
+    assert enum == {"MFG_FP64": 0, "MFG_MIXED": 1, "MFG_MIXED_DF": 2, "MFG_MIXED_TC": 3}
+    base = mi.small(1)["problem"]
+    for name, key in (("fp64", "MFG_FP64"), ("mixed", "MFG_MIXED"), ("mixed_df", "MFG_MIXED_DF"),
+                      ("mixed_tc", "MFG_MIXED_TC")):
+        assert L.problem_struct(base, name).precision == enum[key] == getattr(L, key)
+    with pytest.raises(L.MfgError) as e:
+        L.mfg_plan(dict(base), precision=7)
+    assert e.value.code == L.MFG_ERR_INVALID_ARG
