@@ -87,3 +87,43 @@ def test_lu_and_modal_agree():
     r1 = Solver(p, inst["m0"], inst["V"], inst["W"], method="lu").run(inst["y0"], iters=25)
     r2 = Solver(p, inst["m0"], inst["V"], inst["W"], method="modal").run(inst["y0"], iters=25)
     assert np.linalg.norm(r1["y"] - r2["y"]) <= 1e-10 * np.linalg.norm(r1["y"])
+
+
+def _small_cp_problem(**kw):
+    import mfg_inputs as mi
+    inst = mi.small(7, dim=2, nx=8, ny=12, nt=10, bc=("periodic", "neumann"), **kw)
+    return inst
+
+
+def test_pcg_inner_solve_matches_exact_solve():
+    """The inexact inner solve of Sec. 5 (PCG with the paper's P, warm start)
+    reproduces the exact-solve iterate when its tolerance is at round-off, for
+    both stop references and both time transforms."""
+    import numpy as np
+    from oracle.cp import Solver
+    for l in (1, 2):
+        inst = _small_cp_problem(l=l)
+        p = dict(inst["problem"], cg_tol=1e-13, cg_rule=0)
+        ref = Solver(p, inst["m0"], inst["V"], inst["W"], method="lu").run(inst["y0"], iters=15)
+        for cg_ref in ("resid", "rhs"):
+            got = Solver(p, inst["m0"], inst["V"], inst["W"], method="pcg", cg_ref=cg_ref).run(inst["y0"], iters=15)
+            assert np.linalg.norm(got["y"] - ref["y"]) <= 1e-9 * np.linalg.norm(ref["y"])
+            assert len(got["cg"]) == 15 and min(got["cg"]) >= 1
+
+
+def test_pcg_inner_solve_counts():
+    """Stop relative to the full right-hand side never needs more iterations
+    than stop relative to the warm-start residual (the full right-hand side is
+    the larger reference once z is warm); with nu = 0 and l = 1, P equals
+    C C^T (Sec. 4.2) and every solve takes at most one iteration."""
+    import numpy as np
+    from oracle.cp import Solver
+    inst = _small_cp_problem(l=1)
+    p = dict(inst["problem"], cg_rule=1, cg_tol=1e-10)
+    a = Solver(p, inst["m0"], inst["V"], inst["W"], method="pcg", cg_ref="resid").run(inst["y0"], iters=20)
+    b = Solver(p, inst["m0"], inst["V"], inst["W"], method="pcg", cg_ref="rhs").run(inst["y0"], iters=20)
+    assert sum(b["cg"]) <= sum(a["cg"])
+    inst0 = _small_cp_problem(l=1, nu=0.0)
+    p0 = dict(inst0["problem"], cg_rule=0, cg_tol=1e-12)
+    c = Solver(p0, inst0["m0"], inst0["V"], inst0["W"], method="pcg").run(inst0["y0"], iters=5)
+    assert max(c["cg"]) <= 1
