@@ -166,7 +166,10 @@ int mfg_apply_precond(mfg_plan_t plan, int b, const double* r, double* z, void* 
 int mfg_prox(mfg_plan_t plan, int b, double tau, const double* v, const double* V,
              const double* W, double* y, void* stream);
 
-/* q = C C^T p (eq. largeA) for instance b; p, q: n elements, no aliasing. */
+/* q = C C^T p (eq. largeA) for instance b; p, q: n elements, no aliasing.
+ * Two passes through 2n doubles of the plan's workspace, so it must not run
+ * concurrently with mfg_solve or mfg_adjoint on the same plan (a plan is not
+ * safe for concurrent use from two streams). */
 int mfg_apply_AAt(mfg_plan_t plan, int b, const double* p, double* q, void* stream);
 
 /* r = C v (eq. ABC, reduced: the m0 term excluded) for instance b; v: c*n, r: n. */
