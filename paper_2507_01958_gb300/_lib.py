@@ -92,7 +92,11 @@ def _check(rc):
 
 
 def problem_struct(d, precision=None):
-    """mfg_problem from a problem dict (keys as in mfg_inputs)."""
+    """mfg_problem from a problem dict (keys as in mfg_inputs).  precision (the
+    argument, else d["precision"], else "fp64"): "fp64" (MFG_FP64), "mixed"
+    (FP32 preconditioner, MFG_MIXED), "mixed_tc" (its time transforms on the
+    tensor cores, MFG_MIXED_TC), "mixed_df" (double-float AAt, MFG_MIXED_DF),
+    or the integer code."""
     p = MfgProblem()
     p.dim = d["dim"]
     p.n[0], p.n[1] = d["n"]
