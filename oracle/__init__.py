@@ -17,4 +17,17 @@ Contents (paper sections in brackets):
 Every function is pinned by the CPU test-suite against facts fixed by the paper
 or by mathematics (identities, closed forms, brute force); see the per-function
 docstrings for the pin.
+
+set_threads(k) sets how many host threads the FFTs and the C copy of the prox
+bisection use (default: all cores); results do not depend on it.
 """
+import os as _os
+
+
+def set_threads(k=None):
+    """Host threads for scipy.fft and the C prox (None: os.cpu_count())."""
+    from . import prox, solvers
+    k = int(k or _os.cpu_count() or 1)
+    solvers._WORKERS = k
+    prox._THREADS = k
+    return k

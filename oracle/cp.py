@@ -10,7 +10,9 @@ step sizes of Sec. 5), in the paper's notation and order:
   r_l = ||m_{l+1} - m_l||_2; stop when r_l <= cp_tol (if cp_tol > 0).
 
 The proxes of iteration l use (tau_l, sigma_l) and the step sizes are updated
-afterwards (Chambolle-Pock 2011, Alg. 2).  The dual x is stored explicitly; the
+afterwards (Chambolle-Pock 2011, Alg. 2).  C and C^T are sparse matrices, or on
+grids too large to assemble (n > 2^22) the plane-by-plane applies of
+operators.py, pinned against the sparse matrices.  The dual x is stored explicitly; the
 solve with C C^T is exact (sparse LU or the spatially-diagonalised solver), or,
 with method="pcg", inexact as in Sec. 5: preconditioned CG with the paper's P
 (eq. prec; P = C C^T for l = 0), started from the previous z, stopped at the
@@ -29,15 +31,32 @@ from . import solvers
 from .prox import prox
 
 
+class _PlaneOp:
+    """C or C^T applied plane by plane (operators.apply_C_planes /
+    apply_Ct_planes) for grids too large to assemble; supports `@`."""
+
+    def __init__(self, prob, transpose):
+        self.prob, self.transpose = prob, transpose
+
+    def __matmul__(self, v):
+        f = ops.apply_Ct_planes if self.transpose else ops.apply_C_planes
+        return f(self.prob, v)
+
+
 class Solver:
-    def __init__(self, prob, m0, V, W, method="auto", cg_ref="resid"):
+    def __init__(self, prob, m0, V, W, method="auto", cg_ref="resid", matrix_free=None):
         self.prob = prob
-        self.C = ops.constraint(prob)
-        self.CT = self.C.T.tocsr()
-        self.d = ops.rhs_d(prob, m0)
-        self.V, self.W = V, W
         s, n, c = ops.sizes(prob)
         self.n, self.c = n, c
+        if matrix_free is None:
+            matrix_free = n > (1 << 22)
+        if matrix_free:
+            self.C, self.CT = _PlaneOp(prob, False), _PlaneOp(prob, True)
+        else:
+            self.C = ops.constraint(prob)
+            self.CT = self.C.T.tocsr()
+        self.d = ops.rhs_d(prob, m0)
+        self.V, self.W = V, W
         if method == "auto":
             method = "lu" if n <= 40000 else "modal"
         self.method = method

@@ -100,6 +100,44 @@ def constraint(prob):
     return sp.hstack([A_red] + Bcols).tocsr()
 
 
+def apply_C_planes(prob, v):
+    """C v without assembling C (for grids too large to assemble): plane by
+    plane, row k = L m^{k+1} - m^k/dt + div_h w^k with the m^0 term excluded
+    (it belongs to d), using the spatial blocks B, K of `spatial`.  Pinned
+    against `constraint(prob) @ v` on small grids."""
+    nt = prob["nt"]
+    B, K = spatial(prob)
+    s = K.shape[0]
+    c = n_planes(prob)
+    v = np.asarray(v, dtype=np.float64).reshape(c, nt, s)
+    m = v[0]
+    w = np.concatenate([v[q] for q in range(1, c)], axis=1)  # (nt, (c-1) s) in the w order of B
+    h = dt(prob)
+    out = prob["nu"] * (K @ m.T).T + m / h + (B @ w.T).T
+    out[1:] -= m[:-1] / h
+    return out.reshape(-1)
+
+
+def apply_Ct_planes(prob, p):
+    """C^T p without assembling C: the m rows L p^k - p^{k+1}/dt (p^{Nt} = 0)
+    and the w rows B^T p^k, plane by plane.  Pinned against
+    `constraint(prob).T @ p` on small grids."""
+    nt = prob["nt"]
+    B, K = spatial(prob)
+    s = K.shape[0]
+    c = n_planes(prob)
+    p = np.asarray(p, dtype=np.float64).reshape(nt, s)
+    h = dt(prob)
+    xm = prob["nu"] * (K @ p.T).T + p / h
+    xm[:-1] -= p[1:] / h
+    xw = (B.T @ p.T).T  # (nt, (c-1) s)
+    out = np.empty((c, nt, s))
+    out[0] = xm
+    for q in range(1, c):
+        out[q] = xw[:, (q - 1) * s:q * s]
+    return out.reshape(-1)
+
+
 def rhs_d(prob, m0):
     """d = (m0/dt, 0, ..., 0): the initial datum moved to the right-hand side."""
     nx, ny = prob["n"]

@@ -21,9 +21,52 @@ minimisation of the definition on random cells (tests).
 """
 from __future__ import annotations
 
+import ctypes
+import os
+import subprocess
+
 import numpy as np
 
 from .operators import dt
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "prox_bisect.c")
+_SO = os.path.join(_HERE, "_build", "liboracle_prox.so")
+_clib = None
+_THREADS = os.cpu_count() or 1
+
+
+def build_c():
+    """Compiles prox_bisect.c (the same bisection in plain C, for full-size
+    runs) with every operation separately rounded (-ffp-contract=off); returns
+    the library path, or None if no C compiler is available."""
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    tmp = _SO + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lpthread"]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True)
+    except OSError:
+        return None
+    if r.returncode != 0:
+        return None
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _c_library():
+    global _clib
+    if _clib is None:
+        if not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+            if build_c() is None:
+                _clib = False
+                return None
+        lib = ctypes.CDLL(_SO)
+        P = ctypes.c_void_p
+        lib.oracle_prox_cells.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_double, P, P,
+                                          ctypes.c_double, P, P, ctypes.c_int, ctypes.c_int]
+        lib.oracle_prox_cells.restype = ctypes.c_int
+        _clib = lib
+    return _clib or None
 
 
 def project_K(wbar):
@@ -57,9 +100,31 @@ def prox(prob, tau, v, V, W, max_iter=4000):
     return prox_cells(tau, v, a, b, c, max_iter)
 
 
-def prox_cells(tau, v, a, b, c, max_iter=4000):
+def prox_cells(tau, v, a, b, c, max_iter=4000, use_c=True):
     """The same map for any set of cells: v of shape (c, ...) with coefficient
-    arrays a, c of shape v.shape[1:] and scalar b."""
+    arrays a, c of shape v.shape[1:] and scalar b.  Runs the plain-C copy of
+    the bisection (prox_bisect.c, identical results, threads over cells) when
+    it can be built, else the NumPy loop below."""
+    v = np.asarray(v, dtype=np.float64)
+    lib = _c_library() if use_c else None
+    if lib is not None and v.shape[0] in (3, 5):
+        shp = v.shape
+        vc = np.ascontiguousarray(v.reshape(shp[0], -1))
+        n = vc.shape[1]
+        ac = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), shp[1:]).reshape(-1))
+        cc = np.ascontiguousarray(np.broadcast_to(np.asarray(c, dtype=np.float64), shp[1:]).reshape(-1))
+        out = np.empty_like(vc)
+        rc = lib.oracle_prox_cells(shp[0] - 1, n, float(tau), vc.ctypes.data, ac.ctypes.data, float(b),
+                                   cc.ctypes.data, out.ctypes.data, int(max_iter), int(_THREADS))
+        if rc != 0:
+            raise RuntimeError("oracle_prox_cells rejected its arguments")
+        return out.reshape(shp)
+    return prox_cells_numpy(tau, v, a, b, c, max_iter)
+
+
+def prox_cells_numpy(tau, v, a, b, c, max_iter=4000):
+    """The bisection over all cells at once in NumPy (the reference the C copy
+    is checked against)."""
     v = np.asarray(v, dtype=np.float64)
     mbar = v[0]
     P = project_K(v[1:])

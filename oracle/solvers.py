@@ -12,11 +12,18 @@ sparse LU on small grids.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import scipy.fft as sfft
+import scipy.linalg as sla
 import scipy.sparse.linalg as spla
 
 from .operators import PERIODIC, dt, spacing
+
+
+# threads of the FFT library (all host cores; the transforms are the same)
+_WORKERS = os.cpu_count() or 1
 
 
 def solve_direct(A, b):
@@ -72,9 +79,9 @@ def to_modes(prob, u):
     axes = [1, 2] if prob["dim"] == 2 else [1]
     for a in axes:
         if prob["bc"][a - 1] == PERIODIC:
-            u = np.fft.fft(u, axis=a)
+            u = sfft.fft(u, axis=a, workers=_WORKERS)
         else:
-            u = sfft.dct(u, type=2, norm="ortho", axis=a)
+            u = sfft.dct(u, type=2, norm="ortho", axis=a, workers=_WORKERS)
     return u
 
 
@@ -82,13 +89,13 @@ def from_modes(prob, u):
     axes = [2, 1] if prob["dim"] == 2 else [1]
     for a in axes:
         if prob["bc"][a - 1] == PERIODIC:
-            u = np.fft.ifft(u, axis=a)
+            u = sfft.ifft(u, axis=a, workers=_WORKERS)
         else:
             if np.iscomplexobj(u):
-                u = sfft.idct(u.real, type=2, norm="ortho", axis=a) + \
-                    1j * sfft.idct(u.imag, type=2, norm="ortho", axis=a)
+                u = sfft.idct(u.real, type=2, norm="ortho", axis=a, workers=_WORKERS) + \
+                    1j * sfft.idct(u.imag, type=2, norm="ortho", axis=a, workers=_WORKERS)
             else:
-                u = sfft.idct(u, type=2, norm="ortho", axis=a)
+                u = sfft.idct(u, type=2, norm="ortho", axis=a, workers=_WORKERS)
     return u
 
 
@@ -146,6 +153,30 @@ def precond_modal(prob, r):
     rh = to_modes(prob, np.asarray(r, dtype=np.float64).reshape(nt, nx, ny))
     zh = thomas(diag, -Lh, rh)
     return np.real(from_modes(prob, zh)).reshape(-1)
+
+
+def eig_range_AAt(prob):
+    """Smallest and largest eigenvalue of AAt (eq. largeA).  In the spatial
+    eigenbasis AAt splits into one symmetric tridiagonal N_t x N_t block per
+    spatial mode (the blocks of solve_AAt_modal), so its spectrum is the union
+    of theirs; each block's extreme eigenvalues come from LAPACK's tridiagonal
+    eigensolver.  Modes with equal Laplacian eigenvalue share a block."""
+    nt, kap, h = _modal_blocks(prob)
+    lo, hi = np.inf, -np.inf
+    for k in np.unique(kap):
+        Ls = prob["nu"] * k + 1.0 / h
+        d = np.full(nt, Ls ** 2 + 2.0 * k)
+        d[1:] += 1.0 / h ** 2
+        e = np.full(nt - 1, -Ls / h)
+        lo = min(lo, sla.eigvalsh_tridiagonal(d, e, select="i", select_range=(0, 0))[0])
+        hi = max(hi, sla.eigvalsh_tridiagonal(d, e, select="i", select_range=(nt - 1, nt - 1))[0])
+    return float(lo), float(hi)
+
+
+def cond_AAt(prob):
+    """2-norm condition number of AAt, from eig_range_AAt."""
+    lo, hi = eig_range_AAt(prob)
+    return hi / lo
 
 
 def tridiag_mult(diag, off, x):

@@ -127,3 +127,20 @@ def test_pcg_inner_solve_counts():
     p0 = dict(inst0["problem"], cg_rule=0, cg_tol=1e-12)
     c = Solver(p0, inst0["m0"], inst0["V"], inst0["W"], method="pcg").run(inst0["y0"], iters=5)
     assert max(c["cg"]) <= 1
+
+
+def test_matrix_free_solver_matches_assembled():
+    """The CP loop with the plane-by-plane C / C^T (used on grids too large to
+    assemble) gives the assembled-matrix iterate to round-off, with any thread
+    count."""
+    import oracle
+    inst = mi.small(7, nx=9, ny=8, nt=6, nu=0.1)
+    p = inst["problem"]
+    a = Solver(p, inst["m0"], inst["V"], inst["W"], method="modal").run(inst["y0"], iters=12)
+    oracle.set_threads(1)
+    try:
+        b = Solver(p, inst["m0"], inst["V"], inst["W"], method="modal", matrix_free=True).run(inst["y0"], iters=12)
+    finally:
+        oracle.set_threads()
+    assert np.linalg.norm(a["y"] - b["y"]) <= 1e-12 * np.linalg.norm(a["y"])
+    assert np.linalg.norm(a["x"] - b["x"]) <= 1e-12 * np.linalg.norm(a["x"])

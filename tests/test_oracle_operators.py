@@ -160,3 +160,16 @@ def test_nonunit_eigenvalues_closed_form():
     ref = np.sort(np.concatenate([mu, np.ones((p["nt"] - 1) * K.shape[0])]))
     np.testing.assert_allclose(ev, ref, atol=1e-9)
     assert ev.max() <= 1.25 + 1e-9
+
+
+@pytest.mark.parametrize("bc", [("periodic", "periodic"), ("neumann", "neumann"), ("periodic", "neumann")])
+@pytest.mark.parametrize("dim", [1, 2])
+def test_planewise_C_and_Ct_match_assembled(bc, dim):
+    """The matrix-free plane-by-plane C and C^T (used at full size) equal the
+    assembled reduced constraint matrix and its transpose."""
+    p = mi.small(29, dim=dim, bc=bc, nx=7, ny=6, nt=5)["problem"]
+    C = ops.constraint(p)
+    v = mi.random_field(C.shape[1], 3)
+    z = mi.random_field(C.shape[0], 4)
+    np.testing.assert_allclose(ops.apply_C_planes(p, v), C @ v, rtol=0, atol=1e-12 * np.abs(C @ v).max())
+    np.testing.assert_allclose(ops.apply_Ct_planes(p, z), C.T @ z, rtol=0, atol=1e-12 * np.abs(C.T @ z).max())

@@ -110,3 +110,28 @@ def test_terminal_plane_carries_g():
     np.testing.assert_allclose(a[:-1], p["f_a"])
     np.testing.assert_allclose(a[-1], p["f_a"] + 0.7 / h)
     np.testing.assert_allclose(c[-1], inst["V"] + inst["W"] / h)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+@pytest.mark.parametrize("f_b", [0.0, 0.7])
+def test_c_bisection_equals_numpy_bisection(dim, f_b):
+    """The plain-C copy of the bisection (used for full-size oracle runs) gives
+    the NumPy loop's result bit for bit: zero branch, interior roots, tiny and
+    large tau, NaN inputs."""
+    from oracle.prox import build_c, prox_cells, prox_cells_numpy
+    if build_c() is None:
+        pytest.skip("no C compiler")
+    rng = np.random.default_rng(17 + dim)
+    ncomp = 1 + 2 * dim
+    for tau in (1e-6, 1e-3, 0.05, 1.0, 7.0, 1e4):
+        v = rng.uniform(-3.0, 3.0, size=(ncomp, 3001))
+        v[0, :1000] += 2.0
+        v[1:, 5] = 0.0
+        v[0, 7] = np.nan
+        v[2, 9] = np.nan
+        a = rng.uniform(0.0, 2.0, size=3001)
+        c = rng.normal(size=3001)
+        r_np = prox_cells_numpy(tau, v, a, f_b, c)
+        r_c = prox_cells(tau, v, a, f_b, c)
+        assert np.array_equal(r_np, r_c, equal_nan=True)
+        assert (r_c[0] == 0).any() and (r_c[0] > 0).any()

@@ -90,3 +90,16 @@ def test_modal_applies_match_sparse(bc, dim):
     Pv, lam = solvers.apply_P_modal(p, v)
     assert np.linalg.norm(Pv - P @ v) <= 1e-12 * np.linalg.norm(P @ v)
     assert lam >= np.abs(np.linalg.eigvalsh(P.toarray())).max() * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("dim", [1, 2])
+def test_eig_range_matches_dense_spectrum(bc, dim):
+    """The per-mode tridiagonal spectrum of AAt equals the dense eigenvalues of
+    the assembled C C^T (extremes, to round-off)."""
+    p = mi.small(23, dim=dim, bc=bc, nx=7, ny=6, nt=5)["problem"]
+    ev = np.linalg.eigvalsh(ops.AAt(p).toarray())
+    lo, hi = solvers.eig_range_AAt(p)
+    assert abs(lo - ev.min()) <= 1e-9 * ev.min()
+    assert abs(hi - ev.max()) <= 1e-12 * ev.max()
+    assert abs(solvers.cond_AAt(p) - ev.max() / ev.min()) <= 1e-8 * ev.max() / ev.min()
