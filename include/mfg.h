@@ -66,6 +66,14 @@ enum { MFG_FP64 = 0, MFG_MIXED = 1, MFG_MIXED_DF = 2, MFG_MIXED_TC = 3 };
 /* PCG tolerance: fixed cg_tol, or the paper's rule
  * min{1e-4, max{1e-6, 1e-4 r}} with r the last CP step (Sec. 5). */
 enum { MFG_CG_FIXED = 0, MFG_CG_ADAPTIVE = 1 };
+/* What the PCG tolerance is relative to (the paper does not say, Sec. 5).
+ * MFG_CG_REF_RHS: ||b||_2 of the system solved in eq. CC*,
+ *   AAt z = C (x_l + sigma ybar_l) - sigma d, i.e. stop when
+ *   ||b - AAt z|| <= tol ||b|| (the usual CG convention; one extra AAt apply
+ *   per CP iteration forms ||b|| = ||AAt z_l + sigma (C ybar_l - d)||).
+ * MFG_CG_REF_RESID: the 2-norm of the residual of the warm start z_l,
+ *   sigma (C ybar_l - d): a stricter stop that does not loosen as z_l grows. */
+enum { MFG_CG_REF_RHS = 0, MFG_CG_REF_RESID = 1 };
 
 /* One instance of (VMFG_h).  Paper symbols in brackets. */
 typedef struct {
@@ -91,6 +99,7 @@ typedef struct {
   double cg_tol;     /* relative PCG tolerance for MFG_CG_FIXED                        */
   int max_cg;        /* PCG iteration cap per solve                                    */
   int precision;     /* MFG_FP64 | MFG_MIXED | MFG_MIXED_DF | MFG_MIXED_TC             */
+  int cg_ref;        /* MFG_CG_REF_RHS (0, the default) | MFG_CG_REF_RESID             */
 } mfg_problem;
 
 /* Per-instance run record.  On entry to mfg_solve, `ell`, `tau`, `sigma` are
@@ -166,6 +175,16 @@ int mfg_apply_precond(mfg_plan_t plan, int b, const double* r, double* z, void* 
 int mfg_prox(mfg_plan_t plan, int b, double tau, const double* v, const double* V,
              const double* W, double* y, void* stream);
 
+/* One primal step of the CP iteration for instance b, with the kernel that
+ * mfg_solve runs for it (Sec. 3 eq. pasosChamPock, step sizes of Sec. 5):
+ * the dual lift x = C^T z, y <- prox_{tau phi}(y - tau x) cell by cell, and the
+ * extrapolation ybar <- y_new + theta (y_new - y_old) with
+ * theta = 1/sqrt(1 + 2 gamma tau).  z: n; y, ybar: c*n, updated in place;
+ * V, W: the instance's fields.  Uses the plan's device scalars, so it must not
+ * run concurrently with mfg_solve on the same plan.  Stream-ordered. */
+int mfg_prox_step(mfg_plan_t plan, int b, double tau, const double* z, double* y, double* ybar,
+                  const double* V, const double* W, void* stream);
+
 /* q = C C^T p (eq. largeA) for instance b; p, q: n elements, no aliasing.
  * Two passes through 2n doubles of the plan's workspace, so it must not run
  * concurrently with mfg_solve or mfg_adjoint on the same plan (a plan is not
@@ -208,6 +227,18 @@ long long mfg_kernel_launches(mfg_plan_t plan);
  * cannot inside graphs with conditional nodes). */
 enum { MFG_LAUNCH_GRAPH = 0, MFG_LAUNCH_EAGER = 1 };
 int mfg_set_launch_mode(mfg_plan_t plan, int mode);
+
+/* Test hook for the failure-detection paths; MFG_INJECT_NONE in normal use.
+ * MFG_INJECT_TC_NO_COMMIT: in the tensor-core time pass of mfg_solve
+ * (MFG_MIXED_TC with N_t in {32, 64, 128}) the elected thread issues neither
+ * the MMAs nor their completion commit, so no tensor-core work is in flight
+ * and the bounded mbarrier wait (4096 polls under this hook) runs out: the
+ * instance ends with MFG_ERR_TIMEOUT after its first CP iteration (outputs
+ * unspecified, as for any timeout) and the call returns normally with the
+ * context still usable.  Applies to the plan's later mfg_solve calls (no
+ * graph rebuild).  Invalid `what`: MFG_ERR_INVALID_ARG. */
+enum { MFG_INJECT_NONE = 0, MFG_INJECT_TC_NO_COMMIT = 1 };
+int mfg_set_fault_injection(mfg_plan_t plan, int what);
 
 /* z = P^{-1} r for the single problem *p, like mfg_apply_precond, but with no
  * plan and no device memory allocation of any kind.  The paper has no

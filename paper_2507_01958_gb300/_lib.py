@@ -19,6 +19,8 @@ MFG_PERIODIC, MFG_NEUMANN = 0, 1
 MFG_FP64, MFG_MIXED, MFG_MIXED_DF, MFG_MIXED_TC = 0, 1, 2, 3
 MFG_CG_FIXED, MFG_CG_ADAPTIVE = 0, 1
 MFG_LAUNCH_GRAPH, MFG_LAUNCH_EAGER = 0, 1
+MFG_CG_REF_RHS, MFG_CG_REF_RESID = 0, 1
+MFG_INJECT_NONE, MFG_INJECT_TC_NO_COMMIT = 0, 1
 
 
 class MfgProblem(C.Structure):
@@ -27,7 +29,8 @@ class MfgProblem(C.Structure):
                 ("f_a", C.c_double), ("f_b", C.c_double), ("g_a", C.c_double), ("l", C.c_int),
                 ("gamma", C.c_double), ("tau0", C.c_double), ("sigma0", C.c_double),
                 ("max_cp", C.c_int), ("cp_tol", C.c_double), ("cg_rule", C.c_int),
-                ("cg_tol", C.c_double), ("max_cg", C.c_int), ("precision", C.c_int)]
+                ("cg_tol", C.c_double), ("max_cg", C.c_int), ("precision", C.c_int),
+                ("cg_ref", C.c_int)]
 
 
 class MfgStats(C.Structure):
@@ -67,6 +70,8 @@ def _load():
         "mfg_set_launch_mode": ([P, I], I),
         "mfg_adjoint": ([P, I, V, V, V, V, V, V, V, D, I, C.POINTER(MfgStats), V], I),
         "mfg_apply_precond_noalloc": ([C.POINTER(MfgProblem), V, V, V], I),
+        "mfg_set_fault_injection": ([P, I], I),
+        "mfg_prox_step": ([P, I, D, V, V, V, V, V, V], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -79,7 +84,11 @@ LIB = _load()
 EXPORTED = ("mfg_plan", "mfg_destroy", "mfg_last_error", "mfg_layout", "mfg_sizes", "mfg_solve",
             "mfg_solve_host", "mfg_apply_precond", "mfg_prox", "mfg_apply_AAt", "mfg_apply_C",
             "mfg_apply_Ct", "mfg_kernel_launches", "mfg_set_launch_mode", "mfg_adjoint",
-            "mfg_apply_precond_noalloc")
+            "mfg_apply_precond_noalloc", "mfg_set_fault_injection", "mfg_prox_step")
+
+
+# statuses a solve reports as its result rather than raising
+_OUTCOMES = (MFG_OK, MFG_ERR_NOT_CONVERGED, MFG_ERR_NONFINITE, MFG_ERR_TIMEOUT)
 
 
 def mfg_last_error():
@@ -96,7 +105,8 @@ def problem_struct(d, precision=None):
     argument, else d["precision"], else "fp64"): "fp64" (MFG_FP64), "mixed"
     (FP32 preconditioner, MFG_MIXED), "mixed_tc" (its time transforms on the
     tensor cores, MFG_MIXED_TC), "mixed_df" (double-float AAt, MFG_MIXED_DF),
-    or the integer code."""
+    or the integer code.  d["cg_ref"] (default "rhs"): "rhs" (MFG_CG_REF_RHS)
+    or "resid" (MFG_CG_REF_RESID), or the integer code."""
     p = MfgProblem()
     p.dim = d["dim"]
     p.n[0], p.n[1] = d["n"]
@@ -110,6 +120,8 @@ def problem_struct(d, precision=None):
     prec = d.get("precision", "fp64") if precision is None else precision
     p.precision = {"fp64": MFG_FP64, "mixed": MFG_MIXED, "mixed_df": MFG_MIXED_DF,
                    "mixed_tc": MFG_MIXED_TC}.get(prec, prec)
+    ref = d.get("cg_ref", "rhs")
+    p.cg_ref = {"rhs": MFG_CG_REF_RHS, "resid": MFG_CG_REF_RESID}.get(ref, ref)
     return p
 
 
@@ -193,13 +205,13 @@ def _stats(plan, stats):
 
 def mfg_solve(plan, m0, V, W, y, ybar, z, stats=None, stream=None):
     """Returns (status, stats array).  Solver outcomes (NOT_CONVERGED,
-    NONFINITE) are returned, other errors raise."""
+    NONFINITE, TIMEOUT) are returned, other errors raise."""
     sz = mfg_sizes(plan)
     stats = _stats(plan, stats)
     rc = LIB.mfg_solve(plan.handle, _ptr(m0, sz["field"]), _ptr(V, sz["field"]), _ptr(W, sz["field"]),
                        _ptr(y, sz["primal"]), _ptr(ybar, sz["primal"]), _ptr(z, sz["dual"]), stats,
                        _stream(stream))
-    if rc not in (MFG_OK, MFG_ERR_NOT_CONVERGED, MFG_ERR_NONFINITE):
+    if rc not in _OUTCOMES:
         _check(rc)
     return rc, stats
 
@@ -211,7 +223,7 @@ def mfg_solve_host(plan, m0, V, W, y, ybar, z, stats=None, stream=None):
                             _ptr(W, sz["field"], False), _ptr(y, sz["primal"], False),
                             _ptr(ybar, sz["primal"], False), _ptr(z, sz["dual"], False), stats,
                             _stream(stream))
-    if rc not in (MFG_OK, MFG_ERR_NOT_CONVERGED, MFG_ERR_NONFINITE):
+    if rc not in _OUTCOMES:
         _check(rc)
     return rc, stats
 
@@ -246,6 +258,14 @@ def mfg_prox(plan, b, tau, v, V, W, y, stream=None):
                         _stream(stream)))
 
 
+def mfg_prox_step(plan, b, tau, z, y, ybar, V, W, stream=None):
+    """One primal CP step in place on y, ybar (see mfg.h)."""
+    lay = mfg_layout(plan, b)
+    cn = lay["n"] * lay["c"]
+    _check(LIB.mfg_prox_step(plan.handle, b, float(tau), _ptr(z, lay["n"]), _ptr(y, cn), _ptr(ybar, cn),
+                             _ptr(V), _ptr(W), _stream(stream)))
+
+
 def mfg_apply_AAt(plan, b, p, q, stream=None):
     n = mfg_layout(plan, b)["n"]
     _check(LIB.mfg_apply_AAt(plan.handle, b, _ptr(p, n), _ptr(q, n), _stream(stream)))
@@ -259,6 +279,13 @@ def mfg_apply_C(plan, b, v, r, stream=None):
 def mfg_apply_Ct(plan, b, p, x, stream=None):
     lay = mfg_layout(plan, b)
     _check(LIB.mfg_apply_Ct(plan.handle, b, _ptr(p, lay["n"]), _ptr(x, lay["n"] * lay["c"]), _stream(stream)))
+
+
+def mfg_set_fault_injection(plan, what):
+    """Test hook of the failure-detection paths (see mfg.h): "none" or
+    "tc_no_commit", or the integer code."""
+    code = {"none": MFG_INJECT_NONE, "tc_no_commit": MFG_INJECT_TC_NO_COMMIT}.get(what, what)
+    _check(LIB.mfg_set_fault_injection(plan.handle, code))
 
 
 def mfg_set_launch_mode(plan, mode):

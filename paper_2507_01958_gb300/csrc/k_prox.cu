@@ -42,7 +42,10 @@ __device__ __forceinline__ float newton_h32(float hi, float B, float hP, float t
 
 // FP64 Newton on h from x = 0 with bisection safeguard: the path for inputs
 // outside the FP32 range of the fast path.
+// A NaN in the cell's data (m_bar, the fluxes, V, W or the dual) comes out as
+// NaN rather than as a bracketed root, so the CP step norm reports it.
 __device__ __noinline__ double newton_h64(double B, double hP, double tau, double a1, double tb, double hi) {
+  if (isnan(B) || isnan(hP)) return __longlong_as_double(0x7ff8000000000000LL);
   double x = 0.0, lo = 0.0;
   for (int it = 0; it < 200; ++it) {
     const double it1 = 1.0 / (x + tau);
@@ -257,7 +260,8 @@ __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const dou
       sc->status = MFG_ERR_NONFINITE;
       sc->cp_done = 1;
     }
-    if (sc->status == MFG_ERR_NONFINITE) sc->cp_done = 1;
+    // a non-finite value or a timed-out device wait ends the instance's solve
+    if (sc->status == MFG_ERR_NONFINITE || sc->status == MFG_ERR_TIMEOUT) sc->cp_done = 1;
     if (sc->cp_tol > 0.0 && r <= sc->cp_tol) sc->cp_done = 1;
     if (use_handle) cudaGraphSetConditional(h, (sc->cp_left > 0 && !sc->cp_done) ? 1u : 0u);
     sc->counter = 0;

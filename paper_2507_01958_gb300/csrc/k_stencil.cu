@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __re
   }
   if (flat_tid() == 0) {
     sc->bnorm2 = tot[0];
+    sc->rr = tot[0];  // ||r_0||^2; the MFG_CG_REF_RHS pass replaces bnorm2 by ||b||^2
     sc->cg_it = 0;
     // The paper's adaptive rule, min{1e-4, max{1e-6, 1e-4 r}} (Sec. 5).
     double tol = sc->cg_tol_fixed;
@@ -252,11 +253,24 @@ __device__ __forceinline__ Cols aat_cols(const Geom& g, int i, int j) {
   return c;
 }
 
+// Last block of a mode-2 pass: ||b||^2 becomes the reference of the relative
+// PCG tolerance; a warm start already inside it needs no PCG iteration.
+__device__ __forceinline__ void stop_reference(DevScalars* sc, double b2) {
+  sc->bnorm2 = b2;
+  if (!isfinite(b2)) {
+    sc->cg_done = 1;
+    if (sc->status == MFG_OK) sc->status = MFG_ERR_NONFINITE;
+  } else if (sc->rr <= sc->cg_tol * sc->cg_tol * b2) {
+    sc->cg_done = 1;
+  }
+  sc->counter = 0;
+}
+
 template <int ACTX>
 __global__ void __launch_bounds__(AJ * AI) k_aat_x(Geom g, AatCoef a, int kc, const double* __restrict__ p,
                                                    double* __restrict__ X, double* __restrict__ KP,
                                                    const DevScalars* sc, int mode) {
-  if (mode == 1 && sc->cg_done) return;
+  if (mode != 0 && sc->cg_done) return;
   const int j = blockIdx.x * AJ + threadIdx.x, i = blockIdx.y * AI + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
   const int k0 = blockIdx.z * kc, k1 = min(g.nt, k0 + kc);
@@ -277,14 +291,18 @@ __global__ void __launch_bounds__(AJ * AI) k_aat_x(Geom g, AatCoef a, int kc, co
 }
 
 // mode 0: q = AAt p.  mode 1 (PCG step): also reduces p.q and sets
-// alpha = rz/(p.q) in the device scalars.
+// alpha = rz/(p.q) in the device scalars.  mode 2 (stop reference of
+// MFG_CG_REF_RHS, once per CP iteration with p = z_l): reduces
+// ||AAt z_l + r0||^2 = ||b||^2 with r0 = `r2`, stores it as the reference of
+// the relative tolerance and stops the solve at once if ||r0|| <= tol ||b||;
+// q is not stored.
 template <int ACTX>
 // 2-D: capped at 64 registers (four 256-thread blocks per SM) to hide the load latency
 __global__ void __launch_bounds__(AJ * AI, ACTX ? 4 : 3) k_aat_q(Geom g, AatCoef a, int kc, const double* __restrict__ X,
                                                    const double* __restrict__ KP, const double* __restrict__ p,
                                                    double* __restrict__ q, double* partials, DevScalars* sc,
-                                                   int mode) {
-  if (mode == 1 && sc->cg_done) return;
+                                                   int mode, const double* __restrict__ r2) {
+  if (mode != 0 && sc->cg_done) return;
   const int j = blockIdx.x * AJ + threadIdx.x, i = blockIdx.y * AI + threadIdx.y;
   double acc = 0.0;
   if (i < g.nx && j < g.ny) {
@@ -300,18 +318,27 @@ __global__ void __launch_bounds__(AJ * AI, ACTX ? 4 : 3) k_aat_q(Geom g, AatCoef
       t = fma(a.idt2, xprev, t);
       t = fma(-2.0, KP[base + row + j], t);
       const double qv = fma(a.c4, xc, -t);
-      q[base + row + j] = qv;
-      if (mode == 1) acc = fma(qv, p[base + row + j], acc);
+      if (mode == 2) {
+        const double bv = qv + r2[base + row + j];
+        acc = fma(bv, bv, acc);
+      } else {
+        q[base + row + j] = qv;
+        if (mode == 1) acc = fma(qv, p[base + row + j], acc);
+      }
       xprev = xc;
       base += g.S;
     }
   }
-  if (mode != 1) return;
+  if (mode == 0) return;
   double part[1] = {acc};
   block_sum<1>(part);
   if (!publish_and_check_last<1>(part, partials, &sc->counter)) return;
   double tot[1];
   gather_partials<1>(partials, tot);
+  if (mode == 2) {
+    if (flat_tid() == 0) stop_reference(sc, tot[0]);
+    return;
+  }
   if (flat_tid() == 0) {
     sc->pq = tot[0];
     if (tot[0] > 0.0 && isfinite(tot[0])) {
@@ -342,7 +369,7 @@ template <int ACTX>
 __global__ void __launch_bounds__(AJ * AI) k_aat_x_df(Geom g, AatCoef ad, int kc, const double* __restrict__ p,
                                                       df* __restrict__ X, df* __restrict__ KP,
                                                       const DevScalars* sc, int mode) {
-  if (mode == 1 && sc->cg_done) return;
+  if (mode != 0 && sc->cg_done) return;
   const int j = blockIdx.x * AJ + threadIdx.x, i = blockIdx.y * AI + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
   const df ax = df_from_double(ad.ax), ay = df_from_double(ad.ay), cK = df_from_double(ad.cK),
@@ -370,8 +397,8 @@ template <int ACTX>
 __global__ void __launch_bounds__(AJ * AI) k_aat_q_df(Geom g, AatCoef ad, int kc, const df* __restrict__ X,
                                                       const df* __restrict__ KP, const double* __restrict__ p,
                                                       double* __restrict__ q, double* partials, DevScalars* sc,
-                                                      int mode) {
-  if (mode == 1 && sc->cg_done) return;
+                                                      int mode, const double* __restrict__ r2) {
+  if (mode != 0 && sc->cg_done) return;
   const int j = blockIdx.x * AJ + threadIdx.x, i = blockIdx.y * AI + threadIdx.y;
   double acc = 0.0;
   if (i < g.nx && j < g.ny) {
@@ -390,18 +417,27 @@ __global__ void __launch_bounds__(AJ * AI) k_aat_q_df(Geom g, AatCoef ad, int kc
       t = df_add(t, df_mul(idt2, xprev));
       t = df_sub(t, df_scale2(KP[base + row + j]));
       const double qv = df_to_double(df_sub(df_mul(c4, xc), t));
-      q[base + row + j] = qv;
-      if (mode == 1) acc = fma(qv, p[base + row + j], acc);
+      if (mode == 2) {
+        const double bv = qv + r2[base + row + j];
+        acc = fma(bv, bv, acc);
+      } else {
+        q[base + row + j] = qv;
+        if (mode == 1) acc = fma(qv, p[base + row + j], acc);
+      }
       xprev = xc;
       base += g.S;
     }
   }
-  if (mode != 1) return;
+  if (mode == 0) return;
   double part[1] = {acc};
   block_sum<1>(part);
   if (!publish_and_check_last<1>(part, partials, &sc->counter)) return;
   double tot[1];
   gather_partials<1>(partials, tot);
+  if (mode == 2) {
+    if (flat_tid() == 0) stop_reference(sc, tot[0]);
+    return;
+  }
   if (flat_tid() == 0) {
     sc->pq = tot[0];
     if (tot[0] > 0.0 && isfinite(tot[0])) {
@@ -416,7 +452,7 @@ __global__ void __launch_bounds__(AJ * AI) k_aat_q_df(Geom g, AatCoef ad, int kc
 }
 
 void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, double* partials,
-                DevScalars* sc, int mode, cudaStream_t s, int df64) {
+                DevScalars* sc, int mode, cudaStream_t s, int df64, const double* r2) {
   const AatCoef a = aat_coef(g);
   const int kc = aat2_chunk(g);
   const dim3 grid = aat2_grid(g, kc), block(AJ, AI);
@@ -425,10 +461,10 @@ void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, doub
     df* KP = X + g.n;
     if (g.actx) {
       k_aat_x_df<1><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
-      k_aat_q_df<1><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
+      k_aat_q_df<1><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode, r2);
     } else {
       k_aat_x_df<0><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
-      k_aat_q_df<0><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
+      k_aat_q_df<0><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode, r2);
     }
     return;
   }
@@ -436,10 +472,10 @@ void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, doub
   double* KP = scratch + g.n;
   if (g.actx) {
     k_aat_x<1><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
-    k_aat_q<1><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
+    k_aat_q<1><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode, r2);
   } else {
     k_aat_x<0><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
-    k_aat_q<0><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
+    k_aat_q<0><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode, r2);
   }
 }
 

@@ -35,6 +35,9 @@ namespace {
 constexpr int kTcTW = 128;      // spatial modes per strip (the MMA's M)
 constexpr int kTcThreads = 256;
 constexpr uint32_t kTcPolls = 1u << 20;  // mbarrier polls before a wait gives up
+// Poll limit under the fault-injection hook (no MMA issued, nothing ever
+// arrives): short, so the test of the timeout path costs milliseconds.
+constexpr uint32_t kTcPollsInjected = 1u << 12;
 // Dynamic shared memory is padded to this size so that one block fits per SM:
 // the tensor-memory columns of all resident blocks then stay within 512.
 constexpr size_t kTcMinSmem = 116 * 1024;
@@ -74,9 +77,9 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Waits for the given phase parity of an mbarrier, giving up after kTcPolls polls.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (uint32_t it = 0; it < kTcPolls; ++it) {
+// Waits for the given phase parity of an mbarrier, giving up after `polls` polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t polls) {
+  for (uint32_t it = 0; it < polls; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -133,6 +136,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               const float* __restrict__ lamt, const float* __restrict__ L1, const float* __restrict__ L2,
               int S, DevScalars* sc) {
   if (sc != nullptr && sc->cg_done) return;
+  // Fault-injection hook (MFG_INJECT_TC_NO_COMMIT): the elected thread issues
+  // neither the MMAs nor their commit, so no tensor-core work is ever in flight
+  // and the bounded completion wait must run out.
+  const bool no_commit = sc != nullptr && sc->inject == MFG_INJECT_TC_NO_COMMIT;
+  const uint32_t polls = no_commit ? kTcPollsInjected : kTcPolls;
   using Sh = TcShape<NT>;
   constexpr int TW = Sh::TW, KC = Sh::KC, NKC = Sh::NKC, HALF = NT / 2;
   constexpr uint32_t LBO_A = Sh::LBO_A, LBO_B = Sh::LBO_B, SBO = Sh::SBO, NCOLS = Sh::NCOLS;
@@ -190,7 +198,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   auto run_mma = [&](uint32_t d, int kc) -> bool {
     proxy_fence();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !no_commit) {
       tc_fence_after();
 #pragma unroll 1
       for (int j = 0; j < KC / 8; ++j) {
@@ -205,7 +213,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       tc_commit(mb);
     }
-    const bool ok = mbar_wait(mb, parity);
+    const bool ok = mbar_wait(mb, parity, polls);
     parity ^= 1u;
     tc_fence_after();
     return __syncthreads_and(ok ? 1 : 0) != 0;
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       sc->status = MFG_ERR_TIMEOUT;
       sc->cg_done = 1;
     }
-    mbar_wait(mb, parity ^ 1u);  // let an MMA still in flight finish (bounded) before freeing its columns
+    mbar_wait(mb, parity ^ 1u, polls);  // let an MMA still in flight finish (bounded) before freeing its columns
   }
   tc_fence_before();
   __syncthreads();

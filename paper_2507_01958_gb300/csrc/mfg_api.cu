@@ -85,6 +85,8 @@ int validate_problem(const mfg_problem& p, int idx) {
     return set_error(MFG_ERR_INVALID_ARG, "cg_rule must be MFG_CG_FIXED or MFG_CG_ADAPTIVE" + at);
   if (p.cg_rule == MFG_CG_FIXED && !(p.cg_tol > 0.0))
     return set_error(MFG_ERR_INVALID_ARG, "cg_tol must be > 0" + at);
+  if (p.cg_ref != MFG_CG_REF_RHS && p.cg_ref != MFG_CG_REF_RESID)
+    return set_error(MFG_ERR_INVALID_ARG, "cg_ref must be MFG_CG_REF_RHS or MFG_CG_REF_RESID" + at);
   if (p.precision != MFG_FP64 && p.precision != MFG_MIXED && p.precision != MFG_MIXED_DF &&
       p.precision != MFG_MIXED_TC)
     return set_error(MFG_ERR_INVALID_ARG,
@@ -145,6 +147,7 @@ struct mfg_plan_s {
   const void* key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaStream_t cap0 = nullptr, cap1 = nullptr;
   int launch_mode = MFG_LAUNCH_GRAPH;
+  int inject = MFG_INJECT_NONE;  // test hook, copied into the device scalars by mfg_solve
   // device staging for mfg_solve_host
   double *h_m0 = nullptr, *h_V = nullptr, *h_W = nullptr, *h_y = nullptr, *h_ybar = nullptr,
          *h_z = nullptr;
@@ -175,8 +178,19 @@ int check_b(mfg_plan_t pl, int b) {
   return MFG_OK;
 }
 
-// kernels per CP iteration outside PCG (rhs, precond, init_p, arm, prox) and per PCG iteration
-int launches_cp(const Inst& in) { return 4 + precond_kernel_count(in.g); }
+// kernels per CP iteration outside PCG (rhs, [stop reference], precond, init_p, arm, prox)
+// and per PCG iteration
+int launches_cp(const Inst& in) {
+  return 4 + precond_kernel_count(in.g) +
+         (in.p.cg_ref == MFG_CG_REF_RHS ? aat_kernel_count(in.p.precision == MFG_MIXED_DF) : 0);
+}
+
+// ||b|| of the system of eq. CC* as the PCG stop reference (MFG_CG_REF_RHS):
+// one AAt apply of the warm start z_l, added to r_0 = sigma (C ybar - d).
+void launch_stop_reference(const Inst& in, const double* z, cudaStream_t s) {
+  if (in.p.cg_ref != MFG_CG_REF_RHS) return;
+  launch_AAt(in.g, z, in.q, in.work64, in.partials, in.sc, 2, s, in.p.precision == MFG_MIXED_DF, in.r);
+}
 int launches_cg(const Inst& in) {
   return 1 + aat_kernel_count(in.p.precision == MFG_MIXED_DF) + precond_step_kernel_count(in.g, in.tabs);
 }
@@ -202,6 +216,7 @@ int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, con
   cudaStream_t s = pl->cap0;
   CK(cudaStreamBeginCaptureToGraph(s, body_cp, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   launch_apply_C(g, ybar, in.r, 1.0, m0, in.partials, in.sc, 1, s);
+  launch_stop_reference(in, z, s);
   launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s);
   launch_init_p(g.n, in.zp, in.pv, in.r, in.partials, in.sc, s);
   launch_scalars_begin(in.sc, hg, 1, s);
@@ -272,9 +287,10 @@ int solve_eager(mfg_plan_t pl, const double* m0, const double* V, const double* 
     double* zb = z + in.dual_off;
     for (int it = 0; it < in.p.max_cp; ++it) {
       launch_apply_C(g, ybb, in.r, 1.0, m0b, in.partials, in.sc, 1, s);
+      launch_stop_reference(in, zb, s);
       launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s);
       launch_init_p(g.n, in.zp, in.pv, in.r, in.partials, in.sc, s);
-      pl->launches += 2 + precond_kernel_count(g);
+      pl->launches += launches_cp(in) - 2;  // the prox is counted below; nothing arms a graph node
       for (;;) {
         CK(cudaMemcpyAsync(&hs, in.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -299,6 +315,14 @@ int solve_eager(mfg_plan_t pl, const double* m0, const double* V, const double* 
 }  // namespace
 
 extern "C" {
+
+int mfg_set_fault_injection(mfg_plan_t pl, int what) {
+  if (!pl) return fail(MFG_ERR_INVALID_ARG, "null plan");
+  if (what != MFG_INJECT_NONE && what != MFG_INJECT_TC_NO_COMMIT)
+    return fail(MFG_ERR_INVALID_ARG, "what must be MFG_INJECT_NONE or MFG_INJECT_TC_NO_COMMIT");
+  pl->inject = what;
+  return MFG_OK;
+}
 
 int mfg_set_launch_mode(mfg_plan_t pl, int mode) {
   if (!pl) return fail(MFG_ERR_INVALID_ARG, "null plan");
@@ -437,6 +461,7 @@ int mfg_solve(mfg_plan_t pl, const double* m0, const double* V, const double* W,
     h.max_cg = in.p.max_cg;
     h.cg_rule = in.p.cg_rule;
     h.cg_tol_fixed = in.p.cg_tol;
+    h.inject = pl->inject;
   }
   const bool eager = pl->launch_mode == MFG_LAUNCH_EAGER;
   if (!eager) {
@@ -499,7 +524,8 @@ int mfg_solve_host(mfg_plan_t pl, const double* m0, const double* V, const doubl
   CK(cudaMemcpyAsync(pl->h_ybar, ybar, P, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(pl->h_z, z, D, cudaMemcpyHostToDevice, s));
   int rc = mfg_solve(pl, pl->h_m0, pl->h_V, pl->h_W, pl->h_y, pl->h_ybar, pl->h_z, st, stream);
-  if (rc != MFG_OK && rc != MFG_ERR_NOT_CONVERGED && rc != MFG_ERR_NONFINITE) return rc;
+  if (rc != MFG_OK && rc != MFG_ERR_NOT_CONVERGED && rc != MFG_ERR_NONFINITE && rc != MFG_ERR_TIMEOUT)
+    return rc;
   CK(cudaMemcpyAsync(y, pl->h_y, P, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(ybar, pl->h_ybar, P, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(z, pl->h_z, D, cudaMemcpyDeviceToHost, s));
@@ -588,6 +614,29 @@ int mfg_prox(mfg_plan_t pl, int b, double tau, const double* v, const double* V,
   if (!(tau > 0.0)) return fail(MFG_ERR_INVALID_ARG, "tau must be > 0");
   Inst& in = pl->inst[b];
   launch_prox_plain(in.g, in.cf, tau, v, y, V, W, (cudaStream_t)stream);
+  pl->launches += 1;
+  CK(cudaGetLastError());
+  return MFG_OK;
+}
+
+int mfg_prox_step(mfg_plan_t pl, int b, double tau, const double* z, double* y, double* ybar,
+                  const double* V, const double* W, void* stream) {
+  int rc = check_b(pl, b);
+  if (rc != MFG_OK) return rc;
+  if (!z || !y || !ybar || !V || !W) return fail(MFG_ERR_INVALID_ARG, "null array");
+  if (y == ybar) return fail(MFG_ERR_INVALID_ARG, "y and ybar must be distinct arrays");
+  if (!(tau > 0.0)) return fail(MFG_ERR_INVALID_ARG, "tau must be > 0");
+  Inst& in = pl->inst[b];
+  DevScalars h{};  // pageable: the copy is staged before cudaMemcpyAsync returns
+  h.tau = tau;
+  h.sigma = 1.0;
+  h.theta = 1.0 / std::sqrt(1.0 + 2.0 * in.p.gamma * tau);
+  h.half_itau = 0.5 / tau;
+  h.cp_left = 1;
+  h.status = MFG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(in.sc, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  launch_prox_cp(in.g, in.cf, z, y, ybar, V, W, in.partials, in.sc, 0, 0, s);
   pl->launches += 1;
   CK(cudaGetLastError());
   return MFG_OK;

@@ -55,7 +55,7 @@ struct DevScalars {
   int cg_it, cg_done, max_cg, cg_rule;
   double cg_tol_fixed;
   unsigned int counter;  // last-block ticket
-  unsigned int pad;
+  int inject;            // test hook (mfg_set_fault_injection); 0 in normal runs
 };
 
 // Host helpers (mfg_api.cu): problem validation (sets the error text),
@@ -77,9 +77,10 @@ void launch_apply_C(const Geom& g, const double* v, double* r, double alpha, con
                     const double* pdot = nullptr);
 void launch_apply_Ct(const Geom& g, const double* p, double* x, cudaStream_t s);
 // df64 != 0 selects the double-float variant of the stencil (MFG_MIXED_DF).
-// q = AAt p.  scratch: 2 n doubles (unused by the double-float variant).
+// q = AAt p.  scratch: 2 n doubles.  mode 0: plain apply; 1: PCG step (p.q,
+// alpha); 2: ||AAt p + r2||^2 as the MFG_CG_REF_RHS stop reference (q unused).
 void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, double* partials,
-                DevScalars* sc, int mode, cudaStream_t s, int df64);
+                DevScalars* sc, int mode, cudaStream_t s, int df64, const double* r2 = nullptr);
 int aat_kernel_count(int df64);
 int aat_blocks(const Geom& g);
 

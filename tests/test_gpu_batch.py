@@ -8,7 +8,7 @@ import mfg_inputs as mi
 from oracle import operators as ops
 from oracle.cp import Solver
 
-from _gpu_helpers import dev, host, lib, rel
+from _gpu_helpers import cp_bound, dev, host, lib, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -51,8 +51,7 @@ def test_batch_matches_solo_and_oracle(precision):
         assert np.array_equal(yb, ys) and np.array_equal(zb, zs)
         p = inst["problem"]
         ref = Solver(p, inst["m0"], inst["V"], inst["W"], method="modal").run(inst["y0"], iters=iters)
-        ev = np.linalg.eigvalsh(ops.AAt(p).toarray())
-        tol = max(1e-8, 10 * (ev.max() / ev.min()) * 2.0 ** -53)
+        tol = cp_bound(p)
         assert rel(yb, ref["y"]) <= tol
 
 

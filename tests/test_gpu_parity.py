@@ -20,7 +20,7 @@ from oracle import solvers
 from oracle.cp import Solver
 from oracle.prox import prox as oracle_prox
 
-from _gpu_helpers import dev, host, lib, linf_rel, rel
+from _gpu_helpers import cp_bound, dev, host, lib, linf_rel, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -148,9 +148,9 @@ def test_prox(case):
         assert np.all(got[:n] >= 0)
 
 
-def _gpu_cp(inst, iters, precision="fp64", cg_tol=1e-10):
+def _gpu_cp(inst, iters, precision="fp64", cg_tol=1e-10, **kw):
     import torch
-    p = dict(inst["problem"], max_cp=iters, cg_tol=cg_tol)
+    p = dict(inst["problem"], max_cp=iters, cg_tol=cg_tol, **kw)
     L = lib()
     plan = L.mfg_plan(p, precision=precision)
     y = dev(inst["y0"])
@@ -176,8 +176,7 @@ def test_cp_iterate(case, precision):
     assert rc == 0 and st.status == 0
     assert st.cp_iters == iters and st.ell == iters
     ref = Solver(p, inst["m0"], inst["V"], inst["W"], method="modal").run(inst["y0"], iters=iters)
-    ev = np.linalg.eigvalsh(ops.AAt(p).toarray())
-    tol = max(1e-8, 10 * (ev.max() / ev.min()) * 2.0 ** -53)
+    tol = cp_bound(p)
     n = ops.sizes(p)[1]
     assert rel(y, ref["y"]) <= tol
     assert rel(y[:n], ref["y"][0]) <= tol
@@ -279,6 +278,51 @@ def test_cp_exact_time_solve(case, precision):
     if precision == "fp64":
         assert st.max_cg_in_solve <= 2
     ref = Solver(dict(p, l=1), inst["m0"], inst["V"], inst["W"], method="modal").run(inst["y0"], iters=iters)
-    ev = np.linalg.eigvalsh(ops.AAt(p).toarray())
-    tol = max(1e-8, 10 * (ev.max() / ev.min()) * 2.0 ** -53)
+    tol = cp_bound(p)
     assert rel(y, ref["y"]) <= tol
+
+
+@pytest.mark.parametrize("cg_ref", ["rhs", "resid"])
+@pytest.mark.parametrize("case", [CASES[0], CASES[3], POW2[0]])
+def test_pcg_stop_reference(case, cg_ref):
+    """FP64 Fletcher-Reeves PCG with the paper's P against the oracle's PCG
+    (same algorithm, warm start from z_l, tolerance 1e-10 relative to ||b||
+    (MFG_CG_REF_RHS) or to the warm-start residual (MFG_CG_REF_RESID)): the same
+    number of PCG iterations per solve, up to one at a tolerance boundary, and
+    the same iterate."""
+    inst = _inst(case)
+    iters = 8
+    rc, st, y, ybar, z = _gpu_cp(inst, iters, "fp64", cg_tol=1e-10, cg_ref=cg_ref)
+    assert rc == 0 and st.status == 0
+    p = dict(inst["problem"], max_cp=iters, cg_tol=1e-10)
+    ref = Solver(p, inst["m0"], inst["V"], inst["W"], method="pcg", cg_ref=cg_ref).run(inst["y0"], iters=iters)
+    print(f"\n{cg_ref}: device {st.cg_iters} PCG iterations, oracle {sum(ref['cg'])} ({ref['cg']})")
+    assert abs(st.cg_iters - sum(ref["cg"])) <= 1
+    assert abs(st.max_cg_in_solve - max(ref["cg"])) <= 1
+    assert rel(y, ref["y"]) <= 1e-7
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_prox_step_matches_oracle(case):
+    """The in-solve primal step (k_prox_cp: lift x = C^T z, prox of y - tau x,
+    extrapolation) through mfg_prox_step, against the oracle's sparse C^T and
+    bisection prox."""
+    import torch
+    inst = _inst(case)
+    p = inst["problem"]
+    plan = _plan(p)
+    s, n, c = ops.sizes(p)
+    y0 = mi.random_field((c, p["nt"]) + tuple(p["n"]), 81, -1.0, 1.0)
+    y0[0] += 1.0
+    zf = mi.random_field(n, 82, -0.5, 0.5)
+    tau = 0.37
+    y, ybar = dev(y0), torch.empty(c * n, dtype=torch.float64, device="cuda")
+    lib().mfg_prox_step(plan, 0, tau, dev(zf), y, ybar, dev(inst["V"]), dev(inst["W"]))
+    torch.cuda.synchronize()
+    x = ops.constraint(p).T @ zf
+    ref = oracle_prox(p, tau, (y0.reshape(-1) - tau * x).reshape(y0.shape), inst["V"], inst["W"]).reshape(-1)
+    theta = 1.0 / np.sqrt(1.0 + 2.0 * p["gamma"] * tau)
+    ref_bar = ref + theta * (ref - y0.reshape(-1))
+    assert rel(host(y), ref) <= 1e-12
+    assert np.abs(host(y) - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+    assert rel(host(ybar), ref_bar) <= 1e-12

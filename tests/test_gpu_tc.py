@@ -13,7 +13,7 @@ import mfg_inputs as mi
 from oracle import operators as ops
 from oracle.cp import Solver
 
-from _gpu_helpers import dev, host, lib, rel
+from _gpu_helpers import cp_bound, dev, host, lib, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -80,8 +80,7 @@ def test_cp_iterate_tc(case):
     torch.cuda.synchronize()
     assert rc == 0 and st[0].status == 0 and st[0].cp_iters == 25
     ref = Solver(p, inst["m0"], inst["V"], inst["W"], method="modal").run(inst["y0"], iters=25)
-    ev = np.linalg.eigvalsh(ops.AAt(p).toarray())
-    tol = max(1e-8, 10 * (ev.max() / ev.min()) * 2.0 ** -53)
+    tol = cp_bound(p)
     assert rel(host(y), ref["y"]) <= tol
     assert rel(host(ybar), ref["ybar"]) <= tol
     C = ops.constraint(p)
