@@ -254,12 +254,23 @@ int mfg_set_fault_injection(mfg_plan_t plan, int what);
  *     N_t <= 128; larger problems return MFG_ERR_INVALID_ARG with a message.
  *   - The first call on each device resolves the array's device address and
  *     sets kernel attributes; make that first call before any stream capture.
+ *     First calls from several host threads at once are safe (each resolves
+ *     the same address).  The address is cached for the life of the process:
+ *     after cudaDeviceReset on a device, do not call this entry point again
+ *     there.
  *   - All calls share the array and each call rewrites all of it that it
  *     reads, so no state carries over; but calls whose work overlaps on the
  *     GPU (other streams or other threads) race and corrupt each other.
  *     Calls on one stream are ordered and safe.
- *   - r, z: n device doubles, caller-owned, must not alias.  Precision as in
- *     p->precision.  Stream-ordered; returns after enqueueing. */
+ *   - r, z: n device doubles, caller-owned, must not alias.  Stream-ordered;
+ *     returns after enqueueing.
+ *   - Same passes as mfg_apply_precond: FFT spatial passes on power-of-two
+ *     axes (twiddles are part of the static array), dense ones otherwise.
+ *     p->precision: MFG_FP64 and MFG_MIXED as in a plan, MFG_MIXED_TC with the
+ *     tensor-core time pass as in a plan; MFG_MIXED_DF runs as MFG_MIXED (the
+ *     two differ only in the AAt stencil, which this apply does not use).
+ *     l = 0 (the exact time solve) needs plan-built factors and returns
+ *     MFG_ERR_UNSUPPORTED. */
 int mfg_apply_precond_noalloc(const mfg_problem* p, const double* r, double* z, void* stream);
 
 #ifdef __cplusplus

@@ -28,6 +28,14 @@ struct __align__(2 * sizeof(T)) cx {
 
 enum { FFT_DHT = 0, FFT_DCT2 = 1, FFT_DCT3 = 2 };
 
+// Position of element k of a complex line in shared memory: k with its low
+// four bits XORed by 5 (bits 4-5 of k).  The Stockham stages with span 1 and 4
+// store with a stride of 4 elements, which without it sends 8 lanes of a
+// half-warp to one bank pair; with it every stage's stores and the contiguous
+// loads hit 16 distinct bank pairs per half-warp (8-byte elements).  It
+// permutes within aligned groups of 64, so a line of N >= 8 stays in [0, N).
+__device__ __forceinline__ int swz(int k) { return k ^ (((k >> 4) & 3) * 5); }
+
 template <typename T, int N>
 struct FftShape {
   static constexpr int CL = 8;       // complex lines per block (one per warp)
@@ -98,7 +106,7 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
       real1[l * NP + i] = v;
     } else {
       const int p = (MODE == FFT_DCT2) ? ((i & 1) ? N - 1 - (i >> 1) : (i >> 1)) : i;
-      T* dst = reinterpret_cast<T*>(&buf0[(l >> 1) * NP + p]);
+      T* dst = reinterpret_cast<T*>(&buf0[(l >> 1) * NP + swz(p)]);
       dst[l & 1] = v;
     }
   };
@@ -157,7 +165,7 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
       const T c = dcs[k].x, s = dcs[k].y;
       const T war = c * ak + s * am, wai = s * ak - c * am;
       const T wbr = c * bk + s * bm, wbi = s * bk - c * bm;
-      buf0[q * NP + k] = cx<T>{war - wbi, wai + wbr};
+      buf0[q * NP + swz(k)] = cx<T>{war - wbi, wai + wbr};
     }
     __syncthreads();
   }
@@ -188,17 +196,17 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
       for (int j = lane; j < N / 4; j += 32) {
         const int k = j & (Ns - 1);
         const int m = k * (N / (4 * Ns));
-        const cx<T> a0 = src[j];
-        const cx<T> a1 = cmul(src[j + N / 4], twid(m));
-        const cx<T> a2 = cmul(src[j + N / 2], twid(2 * m));
-        const cx<T> a3 = cmul(src[j + 3 * N / 4], twid(3 * m));
+        const cx<T> a0 = src[swz(j)];
+        const cx<T> a1 = cmul(src[swz(j + N / 4)], twid(m));
+        const cx<T> a2 = cmul(src[swz(j + N / 2)], twid(2 * m));
+        const cx<T> a3 = cmul(src[swz(j + 3 * N / 4)], twid(3 * m));
         const cx<T> s02{a0.x + a2.x, a0.y + a2.y}, d02{a0.x - a2.x, a0.y - a2.y};
         const cx<T> s13{a1.x + a3.x, a1.y + a3.y}, d13{a1.x - a3.x, a1.y - a3.y};
         const int d = ((j - k) << 2) + k;
-        dst[d] = cx<T>{s02.x + s13.x, s02.y + s13.y};
-        dst[d + Ns] = cx<T>{d02.x - sgn * d13.y, d02.y + sgn * d13.x};
-        dst[d + 2 * Ns] = cx<T>{s02.x - s13.x, s02.y - s13.y};
-        dst[d + 3 * Ns] = cx<T>{d02.x + sgn * d13.y, d02.y - sgn * d13.x};
+        dst[swz(d)] = cx<T>{s02.x + s13.x, s02.y + s13.y};
+        dst[swz(d + Ns)] = cx<T>{d02.x - sgn * d13.y, d02.y + sgn * d13.x};
+        dst[swz(d + 2 * Ns)] = cx<T>{s02.x - s13.x, s02.y - s13.y};
+        dst[swz(d + 3 * Ns)] = cx<T>{d02.x + sgn * d13.y, d02.y - sgn * d13.x};
       }
       __syncwarp();
       cx<T>* t = src; src = dst; dst = t;
@@ -206,11 +214,11 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
     if (n2) {
       for (int j = lane; j < N / 2; j += 32) {
         const int k = j & (Ns - 1);
-        const cx<T> a = src[j];
-        const cx<T> b = cmul(src[j + N / 2], twid(k * (N / (2 * Ns))));
+        const cx<T> a = src[swz(j)];
+        const cx<T> b = cmul(src[swz(j + N / 2)], twid(k * (N / (2 * Ns))));
         const int d = ((j - k) << 1) + k;
-        dst[d] = cx<T>{a.x + b.x, a.y + b.y};
-        dst[d + Ns] = cx<T>{a.x - b.x, a.y - b.y};
+        dst[swz(d)] = cx<T>{a.x + b.x, a.y + b.y};
+        dst[swz(d + Ns)] = cx<T>{a.x - b.x, a.y - b.y};
       }
       __syncwarp();
     }
@@ -224,13 +232,13 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
   const T rsn = T(1) / sqrt(T(N));
   for (int idx = tid; idx < CL * N; idx += 256) {
     const int q = idx / N, k = idx % N;
-    const cx<T> zk = Z[q * NP + k];
+    const cx<T> zk = Z[q * NP + swz(k)];
     if (MODE == FFT_DCT3) {
       const int pos = (k < N / 2) ? 2 * k : 2 * (N - 1 - k) + 1;
       R[(2 * q) * NP + pos] = zk.x;
       R[(2 * q + 1) * NP + pos] = zk.y;
     } else {
-      const cx<T> zm = Z[q * NP + ((N - k) & (N - 1))];
+      const cx<T> zm = Z[q * NP + swz((N - k) & (N - 1))];
       const T sr = T(0.5) * (zk.x + zm.x), si = T(0.5) * (zk.y - zm.y);  // X_a
       const T dr = T(0.5) * (zk.y + zm.y), di = T(0.5) * (zm.x - zk.x);  // X_b
       if (MODE == FFT_DHT) {

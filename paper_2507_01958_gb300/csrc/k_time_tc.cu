@@ -38,9 +38,6 @@ constexpr uint32_t kTcPolls = 1u << 20;  // mbarrier polls before a wait gives u
 // Poll limit under the fault-injection hook (no MMA issued, nothing ever
 // arrives): short, so the test of the timeout path costs milliseconds.
 constexpr uint32_t kTcPollsInjected = 1u << 12;
-// Dynamic shared memory is padded to this size so that one block fits per SM:
-// the tensor-memory columns of all resident blocks then stay within 512.
-constexpr size_t kTcMinSmem = 116 * 1024;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -127,7 +124,11 @@ struct TcShape {
   static constexpr uint32_t LBO_A = 16u * TW, LBO_B = 16u * NT, SBO = 128u;
   static constexpr uint32_t NCOLS = 2u * NT;    // two F32 accumulators of N_t columns
   static constexpr size_t floats = 2u * TW * KC + 2u * NT * NT + 2u * TW + NT;
-  static constexpr size_t smem = floats * 4 > kTcMinSmem ? floats * 4 : kTcMinSmem;
+  static constexpr size_t smem = floats * 4;
+  // Shared memory limits the blocks per SM to 1 (N_t = 128), 2 (64) or 5 (32),
+  // so the tensor-memory columns of the resident blocks (NCOLS each) never
+  // exceed the SM's 512, even with blocks of other N_t beside them.
+  static_assert((228u * 1024u / (smem + 1024u)) * NCOLS <= 512u, "TMEM columns of co-resident blocks");
 };
 
 template <int NT>
@@ -193,9 +194,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   bool failed = false;
   const int nstrips = (S + TW - 1) / TW;
 
-  // One product D = A B over the staged K chunk kc (A holds time columns
-  // [kc*KC, kc*KC + KC)); returns false if its completion never arrived.
-  auto run_mma = [&](uint32_t d, int kc) -> bool {
+  // Issue of one product D (+)= A B over the staged K chunk kc (A holds time
+  // columns [kc*KC, kc*KC + KC)) by the elected thread, and the bounded wait for
+  // its completion (false if it never arrived).  Between the two, the block
+  // issues the global loads of the next chunk, so they run under the MMAs.
+  auto issue_mma = [&](uint32_t d, int kc) {
     proxy_fence();
     __syncthreads();
     if (tid == 0 && !no_commit) {
@@ -213,12 +216,54 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       tc_commit(mb);
     }
+  };
+  auto wait_mma = [&]() -> bool {
     const bool ok = mbar_wait(mb, parity, polls);
     parity ^= 1u;
     tc_fence_after();
     return __syncthreads_and(ok ? 1 : 0) != 0;
   };
+  auto run_mma = [&](uint32_t d, int kc) -> bool {
+    issue_mma(d, kc);
+    return wait_mma();
+  };
 
+  // A operand chunks: K chunk kc (times [kc*KC, kc*KC + KC)) of the strip st's
+  // modes, loaded into registers (consecutive threads: consecutive modes, so
+  // every load instruction is coalesced), zero past the last mode or strip.
+  constexpr int IT = TW * KC / 4 / kTcThreads;
+  static_assert(IT * kTcThreads * 4 == TW * KC, "whole float4 groups per thread");
+  auto load_chunk = [&](int st, int kc, float (&x)[IT][4]) {
+    const int s0_ = st * TW;
+    const bool live = st < nstrips;
+#pragma unroll
+    for (int u = 0; u < IT; ++u) {
+      const int q = tid + u * kTcThreads;
+      const int mm = q % TW, kq = q / TW;
+      const int s = s0_ + mm;
+      const int k0 = kc * KC + 4 * kq;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[u][i] = (live && s < S) ? in[(long long)(k0 + i) * S + s] : 0.0f;
+    }
+  };
+  auto stage_chunk = [&](const float (&x)[IT][4]) {
+#pragma unroll
+    for (int u = 0; u < IT; ++u) {
+      const int q = tid + u * kTcThreads;
+      const int mm = q % TW, kq = q / TW;
+      float4 h, l;
+      split4(x[u], h, l);
+      const uint32_t off = kq * LBO_A + (mm >> 3) * 128u + (mm & 7) * 16u;
+      *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Ahi) + off) = h;
+      *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Alo) + off) = l;
+    }
+  };
+
+  // The chunk to stage next, loaded one step ahead: during the previous chunk's
+  // MMAs, or (the first chunk of the next strip) during the current strip's
+  // division, second product and stores.
+  float xr[IT][4];
+  load_chunk(blockIdx.x, 0, xr);
   for (int strip = blockIdx.x; strip < nstrips; strip += gridDim.x) {
     const int s0 = strip * TW;
     const bool own = s0 + m < S;
@@ -230,30 +275,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       // ---- product 1: D1[m][r] = sum_k X[k][s0 + m] V[r][k]
       for (int kc = 0; kc < NKC && !failed; ++kc) {
-        // every load of the chunk is issued before the first shared-memory store
-        constexpr int IT = TW * KC / 4 / kTcThreads;
-        static_assert(IT * kTcThreads * 4 == TW * KC, "whole float4 groups per thread");
-        float x[IT][4];
-#pragma unroll
-        for (int u = 0; u < IT; ++u) {
-          const int q = tid + u * kTcThreads;
-          const int mm = q % TW, kq = q / TW;  // consecutive threads: consecutive modes
-          const int s = s0 + mm;
-          const int k0 = kc * KC + 4 * kq;
-#pragma unroll
-          for (int i = 0; i < 4; ++i) x[u][i] = s < S ? in[(long long)(k0 + i) * S + s] : 0.0f;
-        }
-#pragma unroll
-        for (int u = 0; u < IT; ++u) {
-          const int q = tid + u * kTcThreads;
-          const int mm = q % TW, kq = q / TW;
-          float4 h, l;
-          split4(x[u], h, l);
-          const uint32_t off = kq * LBO_A + (mm >> 3) * 128u + (mm & 7) * 16u;
-          *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Ahi) + off) = h;
-          *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Alo) + off) = l;
-        }
-        failed = !run_mma(d1, kc);
+        stage_chunk(xr);
+        issue_mma(d1, kc);
+        if (kc + 1 < NKC)
+          load_chunk(strip, kc + 1, xr);
+        else
+          load_chunk(strip + gridDim.x, 0, xr);
+        failed = !wait_mma();
       }
     }
     if (!failed) {
@@ -321,11 +349,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+// Resident blocks per SM of each instantiation (set by time_tc_configure).
+int g_tc_blocks_per_sm[3] = {1, 1, 1};
+
 template <int NT>
 void launch_tc(const float* in, float* out, const float* V, const float* lamt, const float* L1, const float* L2,
                int S, DevScalars* sc, cudaStream_t s) {
   const int nstrips = (S + kTcTW - 1) / kTcTW;
-  const int blocks = nstrips < 152 ? nstrips : 152;
+  const int per_sm = g_tc_blocks_per_sm[NT == 32 ? 0 : (NT == 64 ? 1 : 2)];
+  const int cap = 152 * per_sm;  // one wave of resident blocks; each walks strips
+  const int blocks = nstrips < cap ? nstrips : cap;
   k_time_tc<NT><<<blocks, kTcThreads, TcShape<NT>::smem, s>>>(in, out, V, lamt, L1, L2, S, sc);
 }
 
@@ -349,6 +382,19 @@ int time_tc_configure() {
                               (int)TcShape<64>::smem) != cudaSuccess;
   bad |= cudaFuncSetAttribute(k_time_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)TcShape<128>::smem) != cudaSuccess;
+  int occ[3] = {1, 1, 1};
+  bad |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_time_tc<32>, kTcThreads, TcShape<32>::smem) !=
+         cudaSuccess;
+  bad |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_time_tc<64>, kTcThreads, TcShape<64>::smem) !=
+         cudaSuccess;
+  bad |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_time_tc<128>, kTcThreads, TcShape<128>::smem) !=
+         cudaSuccess;
+  const int cols[3] = {64, 128, 256};
+  for (int i = 0; i < 3; ++i) {
+    int b = occ[i] < 1 ? 1 : occ[i];
+    if (b * cols[i] > 512) b = 512 / cols[i];
+    g_tc_blocks_per_sm[i] = b;
+  }
   return bad ? MFG_ERR_CUDA : MFG_OK;
 }
 

@@ -62,6 +62,42 @@ def test_noalloc_matches_plan_entry_point(precision, eta, fwd):
     assert np.array_equal(host(z2), a)
 
 
+# at the limits of the static scratch: n = 2^18 with a 256-point axis, N_t = 128,
+# and the 1-D geometry; power-of-two axes take the FFT spatial passes, whose
+# twiddles live in the static array too
+LIMITS = [
+    dict(seed=4, dim=2, nx=256, ny=256, nt=4, bc=("periodic", "neumann"), l=1),
+    dict(seed=5, dim=2, nx=32, ny=64, nt=128, bc=("neumann", "periodic"), l=1),
+    dict(seed=6, dim=1, nx=256, nt=128, bc=("neumann", "periodic"), l=2),
+]
+
+
+@pytest.mark.parametrize("case", LIMITS)
+@pytest.mark.parametrize("precision,eta,fwd", [("fp64", 1e-12, 1e-8), ("mixed", 5e-5, 1e-2),
+                                               ("mixed_tc", 5e-5, 1e-2)])
+def test_noalloc_at_the_limits(case, precision, eta, fwd):
+    """Same checks as above at the largest problems the static array takes:
+    against the plan entry point and the oracle's assembled P, two calls in a
+    row (the second on a different right-hand side)."""
+    import torch
+    L = lib()
+    p = dict(mi.small(**case)["problem"], precision=precision)
+    n = ops.sizes(p)[1]
+    P = ops.precond(p)
+    plan = L.mfg_plan(p)
+    for seed in (91, 92):
+        r = dev(mi.random_field(n, seed))
+        z_na = torch.full((n,), np.nan, dtype=torch.float64, device="cuda")
+        L.mfg_apply_precond_noalloc(p, r, z_na)
+        z_plan = torch.empty(n, dtype=torch.float64, device="cuda")
+        L.mfg_apply_precond(plan, 0, r, z_plan)
+        torch.cuda.synchronize()
+        a, b = host(z_na), host(z_plan)
+        assert np.all(np.isfinite(a))
+        assert rel(a, b) <= fwd
+        assert _backward_error(P, a, host(r)) <= eta
+
+
 def test_noalloc_rejects_oversize():
     """A problem beyond the static scratch (here 2 x 512 x 512 points) is refused
     with MFG_ERR_INVALID_ARG before any kernel runs."""
