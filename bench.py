@@ -231,7 +231,9 @@ def config2_measure(L, dev, stream, precision, cp=CP_PER_STEP, steps=2):
     """The 2-D periodic 128^2 x 64 workload, four viscosities in one plan."""
     insts = [mi.config2(nu=nu) for nu in mi.CONFIG2_NU]
     probs = [dict(i["problem"], max_cp=cp, cg_tol=CG_TOL, precision=precision) for i in insts]
-    out = Fixed(L, dev, insts, probs, stream).timed(steps=steps, warmup=1)
+    fx = Fixed(L, dev, insts, probs, stream)
+    L.mfg_autotune(fx.plan, stream=stream)
+    out = fx.timed(steps=steps, warmup=1)
     out["workload"] = ("2-D periodic 128x128, N_t=64, nu in {1e-3,1e-2,1e-1,1} in one plan, "
                        f"{cp} CP iterations per instance per step")
     out["unknowns_cp_iters_per_s"] = out["value"] * 64 * 128 * 128
@@ -245,7 +247,11 @@ def batch_measure(L, dev, stream, precision, count=64, cp=CP_PER_STEP):
     insts = mi.config5(count=count)
     probs = [dict(i["problem"], max_cp=cp, cg_tol=CG_TOL, precision=precision) for i in insts]
     fx = Fixed(L, dev, insts, probs, stream)
+    t0 = time.perf_counter()
+    L.mfg_autotune(fx.plan, stream=stream)
+    tune_s = time.perf_counter() - t0
     out = fx.timed(steps=1, warmup=1)
+    out["autotune_seconds"] = tune_s
     nsum = sum(i["problem"]["nt"] * i["problem"]["n"][0] * i["problem"]["n"][1] for i in insts)
     out["workload"] = f"{count} uneven instances (seeds 100..{100 + count - 1}), {cp} CP iterations each"
     out["unknowns_total"] = nsum
@@ -461,6 +467,9 @@ def run_gpu(args):  # noqa: C901
     stream = torch.cuda.current_stream(dev)
     inst, p = headline_problem(args.precision, cp=args.cp_per_step)
     main = Fixed(L, dev, [inst], [p], stream)
+    if not args.no_autotune:
+        L.mfg_autotune(main.plan, stream=stream)
+    schedule = L.mfg_get_schedule(main.plan, 0)
     if args.eager:
         L.mfg_set_launch_mode(main.plan, "eager")
     n_per = p["nt"] * p["n"][0] * p["n"][1]
@@ -612,6 +621,7 @@ def run_gpu(args):  # noqa: C901
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps},
             "gpu_launches": int(launches),
             "clocks": clk,
+            "schedule": schedule,
         }
         out.update(extras)
         print(json.dumps(out))
@@ -700,6 +710,8 @@ def main(argv=None):
     ap.add_argument("--kernels-only", action="store_true",
                     help="three launches of each standalone hot kernel (for ncu captures)")
     ap.add_argument("--small", action="store_true", help="--kernels-only on the 512^2 x 32 Neumann grid")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch choices instead of the autotuner's measured ones")
     ap.add_argument("--eager", action="store_true",
                     help="issue kernels one by one instead of one graph launch (per-kernel profiling)")
     args = ap.parse_args(argv)

@@ -44,7 +44,7 @@ extern "C" {
 enum mfg_status {
   MFG_OK = 0,
   MFG_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range          */
-  MFG_ERR_UNSUPPORTED = 2,   /* valid in the paper, not built here (e.g. q' != 2)     */
+  MFG_ERR_UNSUPPORTED = 2,   /* valid in the paper, not built here (e.g. N_t > 256)   */
   MFG_ERR_CUDA = 3,          /* a CUDA runtime call failed                            */
   MFG_ERR_NOT_CONVERGED = 4, /* PCG hit max_cg before reaching its tolerance          */
   MFG_ERR_NONFINITE = 5,     /* NaN or Inf appeared in a residual or step             */
@@ -84,7 +84,8 @@ typedef struct {
   int nt;            /* N_t >= 2 time steps                                           */
   double T;          /* horizon T > 0, dt = T/N_t                                      */
   double nu;         /* viscosity nu >= 0                                              */
-  double qprime;     /* Hamiltonian exponent q' of eq. power_hamiltonian; only 2      */
+  double qprime;     /* Hamiltonian exponent q' of eq. power_hamiltonian, in [1.05, 20];
+                        2 takes the fast prox, others a general FP64 root finder    */
   double f_a, f_b;   /* f(x,m) = f_a m + f_b m^2 + V(x); f_a, f_b >= 0 (monotone f)   */
   double g_a;        /* g(x,m) = g_a m + W(x); g_a >= 0                                */
   int l;             /* time preconditioner: 1 = DCT-VIII, 2 = DST-I (Sec. 4.1);
@@ -119,9 +120,10 @@ typedef struct mfg_plan_s* mfg_plan_t;
 
 /* Validates `batch` problems, builds the eigenvalue tables (eq. eigs, Alg. 2)
  * and transform matrices on the host in FP64, uploads them and
- * allocates all device workspace on the current device.  Rejects q' != 2
- * (MFG_ERR_UNSUPPORTED), N_t < 2, N < 2, T <= 0, nu < 0, f_a/f_b/g_a < 0,
- * l not in {0,1,2}, N_t > 256 (UNSUPPORTED).  *out is NULL on failure. */
+ * allocates all device workspace on the current device.  Rejects q' outside
+ * [1.05, 20] (MFG_ERR_UNSUPPORTED), N_t < 2, N < 2, T <= 0, nu < 0,
+ * f_a/f_b/g_a < 0, l not in {0,1,2}, N_t > 256 (UNSUPPORTED).  *out is NULL on
+ * failure. */
 int mfg_plan(const mfg_problem* probs, int batch, mfg_plan_t* out);
 
 /* Frees all plan-owned memory.  NULL is accepted. */
@@ -170,7 +172,8 @@ int mfg_solve_host(mfg_plan_t plan, const double* m0, const double* V,
 int mfg_apply_precond(mfg_plan_t plan, int b, const double* r, double* z, void* stream);
 
 /* y = prox_{tau phi}(v) for instance b, cell by cell (Sec. 3; phi_ij = b_hat +
- * F, plus G/dt on the last plane).  v, y: c*n elements; y == v allowed.
+ * F, plus G/dt on the last plane; b_hat = |w|^q/(q m^{q-1}), q = q'/(q'-1),
+ * Sec. 2).  v, y: c*n elements; y == v allowed.
  * V, W: the instance's fields. */
 int mfg_prox(mfg_plan_t plan, int b, double tau, const double* v, const double* V,
              const double* W, double* y, void* stream);
@@ -207,6 +210,7 @@ int mfg_apply_Ct(mfg_plan_t plan, int b, const double* p, double* x, void* strea
  *   dW     : out, dloss/dW(x), Nx*Ny or NULL dnu: out, dloss/dnu, 1 device double
  *   tol, max_iter: relative tolerance and cap of the adjoint PCG
  *   st     : out; cg_iters = adjoint PCG iterations, r_last = final relative residual
+ * Built for q' = 2 (MFG_ERR_UNSUPPORTED otherwise).
  * The adjoint system is solved through its Schur complement
  * C_A H^{-1} C_A^T with the plan's preconditioner P (eq. prec) inside PCG,
  * H being the per-cell Hessian of phi.  The first call allocates a c*n + n
@@ -227,6 +231,41 @@ long long mfg_kernel_launches(mfg_plan_t plan);
  * cannot inside graphs with conditional nodes). */
 enum { MFG_LAUNCH_GRAPH = 0, MFG_LAUNCH_EAGER = 1 };
 int mfg_set_launch_mode(mfg_plan_t plan, int mode);
+
+/* Launch schedule of one instance.  A new plan uses fixed defaults; the
+ * autotuner replaces them with the fastest of a set of measured candidates.
+ * None of the choices changes the operators (results differ only by the
+ * order of floating-point operations: reduction grids and transform
+ * algorithms). */
+enum { MFG_TIME_TENSOR_CORES = 0, MFG_TIME_CUDA_CORES = 1 };
+typedef struct {
+  int tuned;          /* 1: set by mfg_autotune (timed, or from its per-process cache)  */
+  int measured;       /* 1: this plan's mfg_autotune timed the candidates itself        */
+  int time_pass;      /* MFG_TIME_TENSOR_CORES | MFG_TIME_CUDA_CORES                    */
+  int fft[2];         /* per problem axis: 1 = FFT spatial pass, 0 = dense transform   */
+  int aat_blocks;     /* blocks of the AAt stencil launch                               */
+  int vec_blocks;     /* grid cap of the vector and reduction kernels                   */
+  double precond_us;  /* measured time of the chosen preconditioner step, 0 if none     */
+  double aat_us;      /* measured time of the chosen AAt apply, 0 if none               */
+} mfg_schedule;
+
+/* Autotuner.  For every instance of the plan, times (CUDA events, on
+ * `stream`) the candidate launch choices and keeps the fastest:
+ *   - grid cap of the vector and reduction kernels: 152, 304 or 608 blocks;
+ *   - the preconditioner step (Alg. 1/2 with the fused PCG vector work): time
+ *     pass on the tensor cores or the CUDA cores (MFG_MIXED_TC with N_t in
+ *     {32, 64, 128}), FFT or dense transform pass on each power-of-two axis;
+ *   - AAt stencil launch: 152 x 4, 8 or 16 target blocks.
+ * The choice is cached per process by instance shape (grid, N_t, boundary
+ * conditions, precision, l): a later plan with the same shape takes it
+ * without timing.  Uses the plan's workspace and a temporary n-double buffer
+ * (allocated and freed here), overwrites the plan's device scalars, drops
+ * the cached solve graph, and synchronises `stream`.  Call it before a
+ * solve, not concurrently with one. */
+int mfg_autotune(mfg_plan_t plan, void* stream);
+
+/* The launch schedule instance b currently uses. */
+int mfg_get_schedule(mfg_plan_t plan, int b, mfg_schedule* out);
 
 /* Test hook for the failure-detection paths; MFG_INJECT_NONE in normal use.
  * MFG_INJECT_TC_NO_COMMIT: in the tensor-core time pass of mfg_solve

@@ -211,6 +211,44 @@ def config5(count=64, first_seed=100, **kw):
     return [config5_instance(first_seed + i, **kw) for i in range(count)]
 
 
+def problem1(N=16, nt=None, nu=0.01):
+    """Problem 1 of Sec. 5.1 (crowd aversion on the torus [0,1)^2):
+    f(x, y, m) = (m^2 - sin 2 pi y - sin 2 pi x - cos 4 pi x)/2, i.e. f_a = 0,
+    f_b = 1/2, V = -(sin 2 pi y + sin 2 pi x + cos 4 pi x)/2; m0 = 1, g = 0,
+    gamma = 5e-4; N_x = N_y = N, N_t = 8N (Tables 1-2); the stop rule
+    CPtol = 1e-4 ||m0|| and the adaptive CG rule of Sec. 5."""
+    nt = 8 * N if nt is None else nt
+    prob = _problem(2, N, N, (PERIODIC, PERIODIC), nt, nu, f_a=0.0, f_b=0.5, gamma=5e-4, max_cp=5000,
+                    cg_rule=1)
+    X, Y = nodes(prob)
+    V = -0.5 * (np.sin(2 * np.pi * Y) + np.sin(2 * np.pi * X) + np.cos(4 * np.pi * X))
+    m0 = np.ones((N, N))
+    prob["cp_tol"] = 1e-4 * float(np.linalg.norm(m0))
+    W = np.zeros_like(V)
+    return _inst(prob, m0, V, W, initial_iterate(prob, m0))
+
+
+def problem2(N=16, nt=None, nu=0.01, beta=1e-3):
+    """Problem 2 of Sec. 5.2 (Gaussian final target on the Neumann square
+    [-1/2, 1/2]^2): f = 0, g(x, y, m) = (m - m_bar)/beta with beta = 1e-3 (so
+    g_a = 1/beta, W = -m_bar/beta; G enters the last plane divided by dt),
+    m0 = 3 exp(-2^7 ((x + 1/4)^2 + (y - 1/4)^2)),
+    m_bar = 3 exp(-2^7 ((x - 1/4)^2 + (y + 1/4)^2)) on the interior nodes
+    x_i = -1/2 + i dx, dx = 1/(N+1); gamma = 5e-3; N_t = 8N (Table 3); CPtol
+    = 1e-4 ||m0|| and the adaptive CG rule of Sec. 5."""
+    nt = 8 * N if nt is None else nt
+    prob = _problem(2, N, N, (NEUMANN, NEUMANN), nt, nu, f_a=0.0, f_b=0.0, g_a=1.0 / beta, gamma=5e-3,
+                    max_cp=5000, cg_rule=1)
+    X, Y = nodes(prob)
+    X, Y = X - 0.5, Y - 0.5  # the domain starts at -1/2
+    m0 = 3.0 * np.exp(-2.0 ** 7 * ((X + 0.25) ** 2 + (Y - 0.25) ** 2))
+    mbar = 3.0 * np.exp(-2.0 ** 7 * ((X - 0.25) ** 2 + (Y + 0.25) ** 2))
+    prob["cp_tol"] = 1e-4 * float(np.linalg.norm(m0))
+    V = np.zeros_like(X)
+    W = -mbar / beta
+    return _inst(prob, m0, V, W, initial_iterate(prob, m0), m_target=mbar)
+
+
 def small(seed, dim=2, nx=None, ny=None, nt=None, bc=None, nu=None, l=None,
           f_a=None, g_a=None, eps=1e-2, max_cp=20):
     """Small random instance for parity tests: ragged sizes, random fields."""

@@ -18,6 +18,20 @@ m_hi = max(0, m_bar - tau f_eff(0)) + |P|^2/(2 tau), where h(m_hi) >= 0.
 The oracle brackets the root there and bisects until the bracket cannot shrink
 in FP64.  Pins: closed forms for P = 0, the zero branch, and brute-force
 minimisation of the definition on random cells (tests).
+
+General power Hamiltonian H = |p|^{q'}/q' (eq. power_hamiltonian), q = q'/(q'-1),
+b_hat(m, w) = |w|^q / (q m^{q-1}) (Sec. 2).  For fixed m > 0 the w-part only
+depends on |w| and the cone, so the minimiser is w = rho P/|P| with
+rho = m t and t >= 0 the root of
+  g(t) = m t + tau t^{q-1} - |P| = 0            (d/d rho of the w-part),
+and the envelope theorem gives the scalar equation for m,
+  h_q(m) = m - m_bar + tau f_eff(m) - (tau/q') t(m)^q = 0,
+strictly increasing (t decreases with m).  As m -> 0, t -> t0 = (|P|/tau)^{1/(q-1)}
+and rho -> 0: (0, 0) is the prox when h_q(0) = tau f_eff(0) - m_bar
+- (tau/q') (|P|/tau)^{q'} >= 0; otherwise the root lies in (0, m_hi] with
+m_hi = max(0, m_bar - tau f_eff(0)) + (tau/q') (|P|/tau)^{q'}.  q' = 2 gives the
+equation above (t = |P|/(m + tau)).  prox_cells_q solves it by nested
+bisection (t for each trial m, then m), both until the bracket cannot shrink.
 """
 from __future__ import annotations
 
@@ -94,10 +108,75 @@ def h_eq(m, mbar, P2, tau, a, b, c):
 
 
 def prox(prob, tau, v, V, W, max_iter=4000):
-    """prox_{tau phi}(v) for v of shape (c, nt, Nx, Ny); returns the same shape."""
+    """prox_{tau phi}(v) for v of shape (c, nt, Nx, Ny); returns the same shape.
+    prob["qprime"] (default 2) selects the Hamiltonian's exponent q'."""
     v = np.asarray(v, dtype=np.float64)
     a, b, c = coupling(prob, V, W)
+    qp = float(prob.get("qprime", 2.0))
+    if qp != 2.0:
+        return prox_cells_q(qp, tau, v, a, b, c, max_iter)
     return prox_cells(tau, v, a, b, c, max_iter)
+
+
+def _bisect(fun, lo, hi, max_iter):
+    """Vectorised bisection of an increasing function on [lo, hi] (fun(lo) < 0
+    <= fun(hi) where active) until the midpoint equals an endpoint; returns
+    the endpoint with the smaller |fun|."""
+    lo, hi = lo.copy(), hi.copy()
+    active = np.ones(lo.shape, dtype=bool)
+    for _ in range(max_iter):
+        if not active.any():
+            break
+        mid = lo + 0.5 * (hi - lo)
+        active &= ~((mid <= lo) | (mid >= hi))
+        fm = fun(mid)
+        neg = active & (fm < 0.0)
+        pos = active & ~(fm < 0.0)
+        lo = np.where(neg, mid, lo)
+        hi = np.where(pos, mid, hi)
+    return np.where(np.abs(fun(lo)) < np.abs(fun(hi)), lo, hi)
+
+
+def velocity_q(qprime, tau, m, Pn, max_iter=4000):
+    """t >= 0 with m t + tau t^(q-1) = |P| (q = q'/(q'-1)), by bisection on
+    [0, min(|P|/m, (|P|/tau)^(1/(q-1)))]; m > 0."""
+    q = qprime / (qprime - 1.0)
+    m, Pn = np.broadcast_arrays(np.asarray(m, dtype=np.float64), np.asarray(Pn, dtype=np.float64))
+    hi = np.minimum(Pn / m, (Pn / tau) ** (1.0 / (q - 1.0)))
+    t = _bisect(lambda t: m * t + tau * t ** (q - 1.0) - Pn, np.zeros_like(hi), hi, max_iter)
+    return np.where(Pn > 0, t, 0.0)
+
+
+def prox_cells_q(qprime, tau, v, a, b, c, max_iter=4000):
+    """prox_cells for the Hamiltonian |p|^{q'}/q' (header): nested bisection."""
+    v = np.asarray(v, dtype=np.float64)
+    q = qprime / (qprime - 1.0)
+    shp = v.shape[1:]
+    mbar = v[0]
+    P = project_K(v[1:])
+    Pn = np.sqrt((P * P).sum(axis=0))
+    a = np.broadcast_to(np.asarray(a, dtype=np.float64), shp)
+    c = np.broadcast_to(np.asarray(c, dtype=np.float64), shp)
+    f0 = c
+    lim = (tau / qprime) * (Pn / tau) ** qprime
+    zero = (tau * f0 - mbar - lim) >= 0.0
+    hi = np.maximum(0.0, mbar - tau * f0) + lim
+    lo = np.zeros_like(hi)
+    hi = np.where(zero, 1.0, hi)  # inactive cells: any valid bracket
+
+    def hq(m):
+        mm = np.maximum(m, np.finfo(float).tiny)
+        t = velocity_q(qprime, tau, mm, Pn, max_iter)
+        return m - mbar + tau * (a * m + b * m * m + c) - (tau / qprime) * t ** q
+
+    m = _bisect(hq, lo, hi, max_iter)
+    m = np.where(zero, 0.0, m)
+    t = velocity_q(qprime, tau, np.maximum(m, np.finfo(float).tiny), Pn, max_iter)
+    scale = np.where((Pn > 0) & ~zero, m * t / np.where(Pn > 0, Pn, 1.0), 0.0)
+    out = np.empty_like(v)
+    out[0] = m
+    out[1:] = scale[None] * P
+    return out
 
 
 def prox_cells(tau, v, a, b, c, max_iter=4000, use_c=True):

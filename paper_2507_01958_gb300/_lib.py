@@ -42,6 +42,18 @@ class MfgStats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class MfgSchedule(C.Structure):
+    _fields_ = [("tuned", C.c_int), ("measured", C.c_int), ("time_pass", C.c_int), ("fft", C.c_int * 2),
+                ("aat_blocks", C.c_int), ("vec_blocks", C.c_int), ("precond_us", C.c_double),
+                ("aat_us", C.c_double)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["fft"] = list(self.fft)
+        d["time_pass"] = "tensor_cores" if self.time_pass == 0 else "cuda_cores"
+        return d
+
+
 class MfgError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"mfg error {code}: {msg}")
@@ -72,6 +84,8 @@ def _load():
         "mfg_apply_precond_noalloc": ([C.POINTER(MfgProblem), V, V, V], I),
         "mfg_set_fault_injection": ([P, I], I),
         "mfg_prox_step": ([P, I, D, V, V, V, V, V, V], I),
+        "mfg_autotune": ([P, V], I),
+        "mfg_get_schedule": ([P, I, C.POINTER(MfgSchedule)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -84,7 +98,8 @@ LIB = _load()
 EXPORTED = ("mfg_plan", "mfg_destroy", "mfg_last_error", "mfg_layout", "mfg_sizes", "mfg_solve",
             "mfg_solve_host", "mfg_apply_precond", "mfg_prox", "mfg_apply_AAt", "mfg_apply_C",
             "mfg_apply_Ct", "mfg_kernel_launches", "mfg_set_launch_mode", "mfg_adjoint",
-            "mfg_apply_precond_noalloc", "mfg_set_fault_injection", "mfg_prox_step")
+            "mfg_apply_precond_noalloc", "mfg_set_fault_injection", "mfg_prox_step", "mfg_autotune",
+            "mfg_get_schedule")
 
 
 # statuses a solve reports as its result rather than raising
@@ -279,6 +294,19 @@ def mfg_apply_C(plan, b, v, r, stream=None):
 def mfg_apply_Ct(plan, b, p, x, stream=None):
     lay = mfg_layout(plan, b)
     _check(LIB.mfg_apply_Ct(plan.handle, b, _ptr(p, lay["n"]), _ptr(x, lay["n"] * lay["c"]), _stream(stream)))
+
+
+def mfg_autotune(plan, stream=None):
+    """Times the candidate launch choices of every instance and keeps the
+    fastest (see mfg.h); synchronises the stream."""
+    _check(LIB.mfg_autotune(plan.handle, _stream(stream)))
+
+
+def mfg_get_schedule(plan, b):
+    """The launch schedule instance b uses, as a dict."""
+    out = MfgSchedule()
+    _check(LIB.mfg_get_schedule(plan.handle, b, C.byref(out)))
+    return out.as_dict()
 
 
 def mfg_set_fault_injection(plan, what):

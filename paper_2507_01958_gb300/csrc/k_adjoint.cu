@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_grads(Geom g, const double* __
 
 void launch_hinv(const Geom& g, const Coef& cf, const double* y, const double* u, double* out,
                  cudaStream_t s) {
-  const int nb = red_blocks(g.n);
+  const int nb = red_blocks(g.n, g.vec_blocks);
   if (g.actx)
     k_hinv<1><<<nb, kThreads, 0, s>>>(g, cf, y, u, out);
   else
@@ -180,7 +180,7 @@ void launch_hinv(const Geom& g, const Coef& cf, const double* y, const double* u
 
 void launch_ct_hinv(const Geom& g, const Coef& cf, const double* y, const double* p,
                     const double* gsub, double* out, cudaStream_t s, const DevScalars* sc) {
-  const int nb = red_blocks(g.n);
+  const int nb = red_blocks(g.n, g.vec_blocks);
   if (g.actx)
     k_ct_hinv<1><<<nb, kThreads, 0, s>>>(g, cf, y, p, gsub, out, sc);
   else
@@ -190,7 +190,7 @@ void launch_ct_hinv(const Geom& g, const Coef& cf, const double* y, const double
 void launch_adj_grads(const Geom& g, const double* y, const double* z, const double* eta,
                       const double* mu, double* dm0, double* dV, double* dW, double* dnu,
                       double* partials, DevScalars* sc, cudaStream_t s) {
-  const int nb = red_blocks(g.S);
+  const int nb = red_blocks(g.S, g.vec_blocks);
   k_adj_grads<<<nb, kThreads, 0, s>>>(g, y, z, eta, mu, dm0, dV, dW, dnu, partials, sc);
 }
 

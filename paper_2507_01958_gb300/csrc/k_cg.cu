@@ -193,23 +193,23 @@ __global__ void __launch_bounds__(kThreads) k_update_p(long long n, const double
 }
 
 void launch_init_p(long long n, const double* zp, double* p, const double* r, double* partials,
-                   DevScalars* sc, cudaStream_t s) {
-  k_init_p<<<red_blocks(n), kThreads, 0, s>>>(n, zp, p, r, partials, sc);
+                   DevScalars* sc, cudaStream_t s, int cap) {
+  k_init_p<<<red_blocks(n, cap), kThreads, 0, s>>>(n, zp, p, r, partials, sc);
 }
 void launch_update_zr(long long n, double* z, double* r, const double* p, const double* q,
-                      double* partials, DevScalars* sc, cudaStream_t s) {
-  k_update_zr<<<red_blocks(n), kThreads, 0, s>>>(n, z, r, p, q, partials, sc);
+                      double* partials, DevScalars* sc, cudaStream_t s, int cap) {
+  k_update_zr<<<red_blocks(n, cap), kThreads, 0, s>>>(n, z, r, p, q, partials, sc);
 }
 void launch_dot_beta(long long n, const double* r, const double* zp, const double* q, int flexible,
-                     double* partials, DevScalars* sc, cudaStream_t s) {
+                     double* partials, DevScalars* sc, cudaStream_t s, int cap) {
   if (flexible)
-    k_dot_beta<1><<<red_blocks(n), kThreads, 0, s>>>(n, r, zp, q, partials, sc);
+    k_dot_beta<1><<<red_blocks(n, cap), kThreads, 0, s>>>(n, r, zp, q, partials, sc);
   else
-    k_dot_beta<0><<<red_blocks(n), kThreads, 0, s>>>(n, r, zp, q, partials, sc);
+    k_dot_beta<0><<<red_blocks(n, cap), kThreads, 0, s>>>(n, r, zp, q, partials, sc);
 }
 void launch_update_p(long long n, const double* zp, double* p, DevScalars* sc,
-                     cudaGraphConditionalHandle h, int use_handle, cudaStream_t s) {
-  k_update_p<<<red_blocks(n), kThreads, 0, s>>>(n, zp, p, sc, h, use_handle);
+                     cudaGraphConditionalHandle h, int use_handle, cudaStream_t s, int cap) {
+  k_update_p<<<red_blocks(n, cap), kThreads, 0, s>>>(n, zp, p, sc, h, use_handle);
 }
 
 // Start of a CP iteration inside the graph: arms the inner while-node.

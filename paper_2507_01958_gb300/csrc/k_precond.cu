@@ -574,13 +574,13 @@ static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, c
                           const DevScalars* sc, cudaStream_t s, const PcgDot* dot,
                           const PcgZr* zr, bool tc = false) {
   const long long S = g.S, n = g.n;
-  const bool fy = twy != nullptr && fft_supported(g.ny);
-  const bool fx = twx != nullptr && fft_supported(g.nx);
+  const bool fy = g.fft_y && twy != nullptr && fft_supported(g.ny);
+  const bool fx = g.fft_x && twx != nullptr && fft_supported(g.nx);
   // y forward: axis length ny, contiguous
   if (fy) {
     fft_y_forward<T>(g.ny, g.pery, r, w0, twy, dcty, n / g.ny, sc, s, zr);
   } else {
-    if (zr) launch_update_zr(n, zr->z, zr->r, zr->p, zr->q, zr->partials, zr->sc, s);
+    if (zr) launch_update_zr(n, zr->z, zr->r, zr->p, zr->q, zr->partials, zr->sc, s, g.vec_blocks);
     axis_pass<double, T, T>(r, w0, Hy, g.ny, 1, n / g.ny, 0, sc, s);
   }
   T* a = w0;
@@ -595,7 +595,7 @@ static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, c
   if (thc != nullptr) {
     k_thomas<T><<<(int)((S + 255) / 256), 256, 0, s>>>(a, b, thc, thd, tho, g.nt, (int)S, sc);
   } else if constexpr (sizeof(T) == 4) {
-    if (tc && time_tc_supported(g.nt))
+    if (tc && !g.time_simt && time_tc_supported(g.nt))
       launch_time_tc(a, b, V, lamt, L1, L2, g.nt, (int)S, sc, s);
     else
       time_pass<T>(a, b, V, lamt, L1, L2, g.nt, (int)S, sc, s);
@@ -614,7 +614,7 @@ static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, c
     fft_y_inverse<T>(g.ny, g.pery, a, z, twy, dcty, n / g.ny, sc, s, dot);
   } else {
     axis_pass<T, T, double>(a, z, Hy, g.ny, 1, n / g.ny, 1, sc, s);
-    if (dot) launch_dot_beta(n, dot->r, z, dot->q, dot->flex, dot->partials, dot->sc, s);
+    if (dot) launch_dot_beta(n, dot->r, z, dot->q, dot->flex, dot->partials, dot->sc, s, g.vec_blocks);
   }
 }
 
@@ -635,7 +635,7 @@ int precond_kernel_count(const Geom& g) { return g.nx > 1 ? 5 : 3; }
 
 // Kernels of a preconditioner apply that also runs the PCG update and dot products.
 int precond_step_kernel_count(const Geom& g, const PrecTables& t) {
-  const bool fused = t.twy32 != nullptr && fft_supported(g.ny);
+  const bool fused = g.fft_y && t.twy32 != nullptr && fft_supported(g.ny);
   return precond_kernel_count(g) + (fused ? 0 : 2);
 }
 

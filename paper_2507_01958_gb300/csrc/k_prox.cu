@@ -63,6 +63,83 @@ __device__ __noinline__ double newton_h64(double B, double hP, double tau, doubl
   return x;
 }
 
+// Prox for the general power Hamiltonian |p|^{q'}/q', q = q'/(q'-1), b_hat =
+// |w|^q/(q m^{q-1}) (Sec. 2).  For fixed m > 0 the minimising flux is
+// w = m t P/|P| with t >= 0 the root of g(t) = m t + tau t^{q-1} - |P|, and m
+// is the root of the increasing function
+//   h_q(m) = a1 m + tau b m^2 - B - (tau/q') t(m)^q,
+// h_q'(m) = a1 + 2 tau b m + tau (q-1) t^q / (m + tau (q-1) t^{q-2}),
+// with (0, 0) the prox when h_q(0) = -B - (tau/q') (|P|/tau)^{q'} >= 0 and the
+// root in (0, max(0, B) + (tau/q') (|P|/tau)^{q'}] otherwise.  Both roots by
+// safeguarded Newton in FP64 (the bracket kept by the sign, a bisection step
+// whenever Newton leaves it).  q' = 2 never takes this path.
+__device__ double velocity_q(double m, double Pn, double tau, double q) {
+  double lo = 0.0, hi = fmin(Pn / m, pow(Pn / tau, 1.0 / (q - 1.0)));
+  double t = hi;
+  for (int it = 0; it < 200; ++it) {
+    const double tq2 = pow(t, q - 2.0);
+    const double gt = m * t + tau * tq2 * t - Pn;
+    if (gt < 0.0) lo = t; else hi = t;
+    if (gt == 0.0 || hi - lo <= 4e-16 * hi) break;
+    const double dg = m + tau * (q - 1.0) * tq2;
+    double tn = t - gt / dg;
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    const double step = fabs(tn - t);
+    t = tn;
+    if (step <= 1e-16 * t) break;
+  }
+  return t;
+}
+
+template <int NW>
+__device__ void prox_cell_q(double mbar, const double (&wbar)[NW], double tau, double qp, double a1, double tb,
+                            double c, double& m, double (&w)[NW]) {
+  const double q = qp / (qp - 1.0);
+  double P[NW];
+  double P2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < NW; ++k) {
+    const bool neg = __double_as_longlong(wbar[k]) < 0;
+    P[k] = ((k & 1) ? neg : !neg) ? wbar[k] : 0.0;
+    P2 = fma(P[k], P[k], P2);
+  }
+  const double Pn = sqrt(P2);
+  const double B = fma(-tau, c, mbar);
+  if (isnan(B) || isnan(Pn)) {  // NaN in, NaN out (the CP step norm reports it)
+    m = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+    for (int k = 0; k < NW; ++k) w[k] = m;
+    return;
+  }
+  const double lim = (tau / qp) * pow(Pn / tau, qp);
+  if (-B - lim >= 0.0) {
+    m = 0.0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) w[k] = 0.0;
+    return;
+  }
+  double lo = 0.0, hi = fmax(B, 0.0) + lim;
+  double x = 0.5 * hi, t = 0.0;
+  for (int it = 0; it < 200; ++it) {
+    t = Pn > 0.0 ? velocity_q(x, Pn, tau, q) : 0.0;
+    const double tq = pow(t, q);
+    const double hx = fma(tb, x * x, a1 * x) - B - (tau / qp) * tq;
+    if (hx < 0.0) lo = x; else hi = x;
+    if (hx == 0.0 || hi - lo <= 4e-16 * hi) break;
+    const double dh = fma(2.0 * tb, x, a1) + (Pn > 0.0 ? tau * (q - 1.0) * tq / (x + tau * (q - 1.0) * pow(t, q - 2.0)) : 0.0);
+    double xn = x - hx / dh;
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    const double step = fabs(xn - x);
+    x = xn;
+    if (step <= 1e-16 * x) break;
+  }
+  m = x;
+  t = Pn > 0.0 ? velocity_q(x, Pn, tau, q) : 0.0;
+  const double s = Pn > 0.0 ? x * t / Pn : 0.0;
+#pragma unroll
+  for (int k = 0; k < NW; ++k) w[k] = s * P[k];
+}
+
 // Per-step constants of the prox (tau is the CP primal step).
 struct ProxK {
   double tau, half_tau, half_itau, tb;  // tau, tau/2, 1/(2 tau), tau f_b
@@ -172,7 +249,7 @@ __device__ __forceinline__ void prox_cell(double mbar, const double (&wbar)[NW],
 // on a Neumann axis the neighbour index of an end point is the point itself,
 // so the difference across the end (a flux slot of Sec. 4.3 that does not
 // exist) is zero and K takes its one-sided form.
-template <int ACTX>
+template <int ACTX, bool GENQ>
 __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const double* __restrict__ z,
                                                       double* __restrict__ y, double* __restrict__ ybar,
                                                       const double* __restrict__ V,
@@ -225,8 +302,11 @@ __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const dou
     const long long f = (long long)i * g.ny + j;
     const double cc = last ? fma(W[f], g.idt, V[f]) : V[f];
     double m_new;
-    prox_cell<NW>(mbar, wbar, K, last ? a1_last : a1_in, last ? a1f_last : a1f_in, last ? a1d_last : a1d_in, cc,
-                  m_new, w_new);
+    if constexpr (GENQ)
+      prox_cell_q<NW>(mbar, wbar, tau, cf.qprime, last ? a1_last : a1_in, K.tb, cc, m_new, w_new);
+    else
+      prox_cell<NW>(mbar, wbar, K, last ? a1_last : a1_in, last ? a1f_last : a1f_in, last ? a1d_last : a1d_in, cc,
+                    m_new, w_new);
     const double dm = m_new - m_old;
     y[e] = m_new;
     ybar[e] = fma(theta, dm, m_new);
@@ -268,7 +348,7 @@ __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const dou
   }
 }
 
-template <int ACTX>
+template <int ACTX, bool GENQ>
 __global__ void __launch_bounds__(kThreads) k_prox_plain(Geom g, Coef cf, double tau,
                                                          const double* v, double* y,
                                                          const double* __restrict__ V,
@@ -289,8 +369,11 @@ __global__ void __launch_bounds__(kThreads) k_prox_plain(Geom g, Coef cf, double
     const bool last = (k == g.nt - 1);
     const double cc = last ? fma(W[f], g.idt, V[f]) : V[f];
     double m_new;
-    prox_cell<NW>(v[e], wbar, K, last ? a1_last : a1_in, last ? a1f_last : a1f_in, last ? a1d_last : a1d_in, cc,
-                  m_new, w_new);
+    if constexpr (GENQ)
+      prox_cell_q<NW>(v[e], wbar, tau, cf.qprime, last ? a1_last : a1_in, K.tb, cc, m_new, w_new);
+    else
+      prox_cell<NW>(v[e], wbar, K, last ? a1_last : a1_in, last ? a1f_last : a1f_in, last ? a1d_last : a1d_in, cc,
+                    m_new, w_new);
     y[e] = m_new;
 #pragma unroll
     for (int q = 0; q < NW; ++q) y[e + (q + 1) * n] = w_new[q];
@@ -300,20 +383,34 @@ __global__ void __launch_bounds__(kThreads) k_prox_plain(Geom g, Coef cf, double
 void launch_prox_cp(const Geom& g, const Coef& cf, const double* z, double* y, double* ybar,
                     const double* V, const double* W, double* partials, DevScalars* sc,
                     cudaGraphConditionalHandle h, int use_handle, cudaStream_t s) {
-  const int nb = red_blocks(g.n);
-  if (g.actx)
-    k_prox_cp<1><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle);
-  else
-    k_prox_cp<0><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle);
+  const int nb = red_blocks(g.n, g.vec_blocks);
+  // the general-q' root finder is its own instantiation, so the q' = 2 kernel
+  // keeps its registers
+  if (cf.qprime != 2.0) {
+    if (g.actx)
+      k_prox_cp<1, true><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle);
+    else
+      k_prox_cp<0, true><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle);
+  } else if (g.actx) {
+    k_prox_cp<1, false><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle);
+  } else {
+    k_prox_cp<0, false><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle);
+  }
 }
 
 void launch_prox_plain(const Geom& g, const Coef& cf, double tau, const double* v, double* y,
                        const double* V, const double* W, cudaStream_t s) {
-  const int nb = red_blocks(g.n);
-  if (g.actx)
-    k_prox_plain<1><<<nb, kThreads, 0, s>>>(g, cf, tau, v, y, V, W);
-  else
-    k_prox_plain<0><<<nb, kThreads, 0, s>>>(g, cf, tau, v, y, V, W);
+  const int nb = red_blocks(g.n, g.vec_blocks);
+  if (cf.qprime != 2.0) {
+    if (g.actx)
+      k_prox_plain<1, true><<<nb, kThreads, 0, s>>>(g, cf, tau, v, y, V, W);
+    else
+      k_prox_plain<0, true><<<nb, kThreads, 0, s>>>(g, cf, tau, v, y, V, W);
+  } else if (g.actx) {
+    k_prox_plain<1, false><<<nb, kThreads, 0, s>>>(g, cf, tau, v, y, V, W);
+  } else {
+    k_prox_plain<0, false><<<nb, kThreads, 0, s>>>(g, cf, tau, v, y, V, W);
+  }
 }
 
 }  // namespace mfg

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __re
 
 void launch_apply_C(const Geom& g, const double* v, double* r, double alpha, const double* m0,
                     double* partials, DevScalars* sc, int mode, cudaStream_t s, const double* pdot) {
-  const int nb = red_blocks(g.n);
+  const int nb = red_blocks(g.n, g.vec_blocks);
   if (g.actx)
     k_apply_C<1><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, pdot, partials, sc, mode);
   else
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_Ct(Geom g, const double* __r
 }
 
 void launch_apply_Ct(const Geom& g, const double* p, double* x, cudaStream_t s) {
-  const int nb = red_blocks(g.n);
+  const int nb = red_blocks(g.n, g.vec_blocks);
   if (g.actx)
     k_apply_Ct<1><<<nb, kThreads, 0, s>>>(g, p, x);
   else
@@ -227,7 +227,7 @@ AatCoef aat_coef(const Geom& g) {
 
 int aat2_chunk(const Geom& g) {
   const long long cols = (long long)((g.ny + AJ - 1) / AJ) * ((g.nx + AI - 1) / AI);
-  const long long want = 152 * 8;  // 256-thread blocks: 8 per SM fill it
+  const long long want = g.aat_want;  // default 152 * 8: 256-thread blocks, 8 per SM fill it
   long long chunks = (want + cols - 1) / cols;
   if (chunks < 1) chunks = 1;
   if (chunks > g.nt) chunks = g.nt;

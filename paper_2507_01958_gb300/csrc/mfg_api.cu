@@ -14,8 +14,12 @@
 // Batched instances are independent branches of the same graph, so the
 // runtime may overlap them on the GPU.  All control flow (convergence tests,
 // step sizes) lives in device memory; the host only reads the final record.
+#include <array>
+#include <climits>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -54,6 +58,8 @@ struct Inst {
   double* partials = nullptr;
   DevScalars* sc = nullptr;  // points into the plan's contiguous array
   double *adj_t = nullptr, *adj_eta = nullptr;  // adjoint workspace, allocated on first use
+  int tuned = 0, measured = 0;                  // launch choices from mfg_autotune
+  double tune_precond_us = 0.0, tune_aat_us = 0.0;
 };
 
 }  // namespace
@@ -63,8 +69,8 @@ namespace mfg {
 int validate_problem(const mfg_problem& p, int idx) {
   const std::string at = " (instance " + std::to_string(idx) + ")";
   if (p.dim != 1 && p.dim != 2) return set_error(MFG_ERR_INVALID_ARG, "dim must be 1 or 2" + at);
-  if (p.qprime != 2.0)
-    return set_error(MFG_ERR_UNSUPPORTED, "only the quadratic Hamiltonian q' = 2 is built" + at);
+  if (!(p.qprime >= 1.05 && p.qprime <= 20.0))
+    return set_error(MFG_ERR_UNSUPPORTED, "the Hamiltonian exponent q' must lie in [1.05, 20]" + at);
   for (int a = 0; a < p.dim; ++a) {
     if (p.n[a] < 2) return set_error(MFG_ERR_INVALID_ARG, "grid sizes must be >= 2" + at);
     if (!(p.len[a] > 0.0)) return set_error(MFG_ERR_INVALID_ARG, "domain lengths must be > 0" + at);
@@ -129,6 +135,10 @@ Geom make_geom(const mfg_problem& p) {
   }
   g.S = g.nx * g.ny;
   g.n = (long long)g.S * g.nt;
+  g.vec_blocks = kRedBlocks;
+  g.aat_want = kAatWantDefault;
+  g.time_simt = 0;
+  g.fft_x = g.fft_y = 1;
   return g;
 }
 
@@ -218,7 +228,7 @@ int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, con
   launch_apply_C(g, ybar, in.r, 1.0, m0, in.partials, in.sc, 1, s);
   launch_stop_reference(in, z, s);
   launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s);
-  launch_init_p(g.n, in.zp, in.pv, in.r, in.partials, in.sc, s);
+  launch_init_p(g.n, in.zp, in.pv, in.r, in.partials, in.sc, s, g.vec_blocks);
   launch_scalars_begin(in.sc, hg, 1, s);
   cudaStreamCaptureStatus cst;
   const cudaGraphNode_t* deps = nullptr;
@@ -242,7 +252,7 @@ int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, con
   const PcgZr zr{z, in.r, in.pv, in.q, in.partials, in.sc};
   launch_AAt(g, in.pv, in.q, in.work64, in.partials, in.sc, 1, s2, dfa);
   launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s2, &dot, &zr);
-  launch_update_p(g.n, in.zp, in.pv, in.sc, hg, 1, s2);
+  launch_update_p(g.n, in.zp, in.pv, in.sc, hg, 1, s2, g.vec_blocks);
   CK(cudaStreamEndCapture(s2, &body_cg));
   return MFG_OK;
 }
@@ -289,7 +299,7 @@ int solve_eager(mfg_plan_t pl, const double* m0, const double* V, const double* 
       launch_apply_C(g, ybb, in.r, 1.0, m0b, in.partials, in.sc, 1, s);
       launch_stop_reference(in, zb, s);
       launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s);
-      launch_init_p(g.n, in.zp, in.pv, in.r, in.partials, in.sc, s);
+      launch_init_p(g.n, in.zp, in.pv, in.r, in.partials, in.sc, s, g.vec_blocks);
       pl->launches += launches_cp(in) - 2;  // the prox is counted below; nothing arms a graph node
       for (;;) {
         CK(cudaMemcpyAsync(&hs, in.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -299,7 +309,7 @@ int solve_eager(mfg_plan_t pl, const double* m0, const double* V, const double* 
         const PcgZr zr{zb, in.r, in.pv, in.q, in.partials, in.sc};
         launch_AAt(g, in.pv, in.q, in.work64, in.partials, in.sc, 1, s, dfa);
         launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s, &dot, &zr);
-        launch_update_p(g.n, in.zp, in.pv, in.sc, 0, 0, s);
+        launch_update_p(g.n, in.zp, in.pv, in.sc, 0, 0, s, g.vec_blocks);
         pl->launches += launches_cg(in);
       }
       launch_prox_cp(g, in.cf, zb, yb, ybb, Vb, Wb, in.partials, in.sc, 0, 0, s);
@@ -312,9 +322,220 @@ int solve_eager(mfg_plan_t pl, const double* m0, const double* V, const double* 
   return MFG_OK;
 }
 
+// ------------------------------------------------------------- autotuner --
+// Launch choices per instance shape (grid, N_t, boundary conditions,
+// precision, time solve), measured once per process: a later plan with the
+// same shape takes the cached choice without timing again.
+using TuneKey = std::array<int, 8>;
+struct TuneVal {
+  int vec_blocks, aat_want, time_simt, fft_x, fft_y;
+  double precond_us, aat_us;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+TuneKey tune_key(const Inst& in) {
+  return TuneKey{in.g.nx, in.g.ny, in.g.nt, in.g.perx, in.g.pery, in.p.precision, in.p.l == 0 ? 1 : 0,
+                 in.g.actx};
+}
+
+// Fills a device buffer with a positive, finite pattern (bytes 0x3F), so that
+// timed reductions see nonzero, well-scaled data.
+int fill_pattern(void* p, size_t bytes, cudaStream_t s) {
+  return cudaMemsetAsync(p, 0x3F, bytes, s) == cudaSuccess ? MFG_OK : MFG_ERR_CUDA;
+}
+
+// PCG scalars under which every timed kernel runs its full body: nothing
+// converged, alpha = 0 (the fused z, r update leaves them unchanged).
+int reset_tune_scalars(const Inst& in, cudaStream_t s) {
+  DevScalars h{};
+  h.status = MFG_OK;
+  h.rz = 1.0;
+  h.bnorm2 = 1.0;
+  h.cg_tol = 0.0;
+  h.max_cg = INT_MAX;
+  return cudaMemcpyAsync(in.sc, &h, sizeof(h), cudaMemcpyHostToDevice, s) == cudaSuccess ? MFG_OK : MFG_ERR_CUDA;
+}
+
+// Mean time in microseconds of `f` on stream s (one warm-up call, then enough
+// repetitions for about 2 ms, between 3 and 50).
+template <typename F>
+double time_us(F&& f, cudaStream_t s, cudaEvent_t a, cudaEvent_t b) {
+  f();
+  cudaEventRecord(a, s);
+  f();
+  cudaEventRecord(b, s);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  const double t0 = 1e3 * ms;
+  int reps = t0 > 0 ? (int)std::ceil(2000.0 / t0) : 50;
+  reps = reps < 3 ? 3 : (reps > 50 ? 50 : reps);
+  cudaEventRecord(a, s);
+  for (int i = 0; i < reps; ++i) f();
+  cudaEventRecord(b, s);
+  cudaEventSynchronize(b);
+  cudaEventElapsedTime(&ms, a, b);
+  return 1e3 * ms / reps;
+}
+
+// Times the candidates for one instance and keeps the fastest in in.g:
+//   vector and reduction grid cap    152, 304, 608 blocks
+//   preconditioner passes            time pass on the tensor cores or the CUDA
+//                                    cores (MFG_MIXED_TC); FFT or dense pass per
+//                                    power-of-two axis; timed as the PCG step
+//                                    (fused z, r update and dot products)
+//   AAt stencil target blocks        152 x 4, 8, 16
+int tune_instance(Inst& in, double* zbuf, cudaStream_t s, cudaEvent_t a, cudaEvent_t b) {
+  const long long n = in.g.n;
+  int rc;
+  if ((rc = fill_pattern(in.r, n * 8, s)) || (rc = fill_pattern(in.pv, n * 8, s)) ||
+      (rc = fill_pattern(in.q, n * 8, s)) || (rc = fill_pattern(in.zp, n * 8, s)) ||
+      (rc = fill_pattern(zbuf, n * 8, s)))
+    return rc;
+  const int flex = in.p.precision != MFG_FP64;
+  Geom g = in.g;
+  // vector kernels
+  {
+    double best = 1e300;
+    int choice = g.vec_blocks;
+    for (int cap : {152, 304, 608}) {
+      g.vec_blocks = cap;
+      if ((rc = reset_tune_scalars(in, s))) return rc;
+      const double t = time_us([&] {
+        launch_update_p(n, in.zp, in.pv, in.sc, 0, 0, s, cap);
+        launch_init_p(n, in.zp, in.pv, in.r, in.partials, in.sc, s, cap);
+      }, s, a, b);
+      if (t < best) { best = t; choice = cap; }
+    }
+    g.vec_blocks = choice;
+  }
+  // preconditioner passes
+  {
+    const bool tc_opt = in.p.precision == MFG_MIXED_TC && time_tc_supported(g.nt) && in.p.l != 0;
+    const bool fy_opt = fft_supported(g.ny) && in.tabs.twy32 != nullptr;
+    const bool fx_opt = g.nx > 1 && fft_supported(g.nx) && in.tabs.twx32 != nullptr;
+    double best = 1e300;
+    Geom pick = g;
+    for (int ts = 0; ts <= (tc_opt ? 1 : 0); ++ts)
+      for (int fy = fy_opt ? 1 : 0; fy >= 0; --fy)
+        for (int fx = fx_opt ? 1 : 0; fx >= 0; --fx) {
+          Geom c = g;
+          c.time_simt = tc_opt ? ts : 0;
+          c.fft_y = fy;
+          c.fft_x = fx;
+          const PcgDot dot{in.r, in.q, in.partials, in.sc, flex};
+          const PcgZr zr{zbuf, in.r, in.pv, in.q, in.partials, in.sc};
+          if ((rc = reset_tune_scalars(in, s))) return rc;
+          const double t = time_us([&] {
+            launch_precond(c, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s, &dot, &zr);
+          }, s, a, b);
+          if (t < best) { best = t; pick = c; }
+        }
+    g = pick;
+    in.tune_precond_us = best;
+  }
+  // AAt stencil chunking
+  {
+    double best = 1e300;
+    int choice = g.aat_want;
+    for (int want : {152 * 4, 152 * 8, 152 * 16}) {
+      Geom c = g;
+      c.aat_want = want;
+      if ((rc = reset_tune_scalars(in, s))) return rc;
+      const double t = time_us([&] {
+        launch_AAt(c, in.pv, in.q, in.work64, in.partials, in.sc, 1, s, in.p.precision == MFG_MIXED_DF);
+      }, s, a, b);
+      if (t < best) { best = t; choice = want; }
+    }
+    g.aat_want = choice;
+    in.tune_aat_us = best;
+  }
+  if (cudaGetLastError() != cudaSuccess) return fail(MFG_ERR_CUDA, "a launch failed while autotuning");
+  in.g = g;
+  in.measured = 1;
+  in.tuned = 1;
+  return MFG_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int mfg_autotune(mfg_plan_t pl, void* stream) {
+  if (!pl) return fail(MFG_ERR_INVALID_ARG, "null plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t nmax = 0;
+  for (auto& in : pl->inst) nmax = std::max(nmax, (size_t)in.g.n);
+  double* zbuf = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaMalloc(&zbuf, nmax * 8) != cudaSuccess) return fail(MFG_ERR_CUDA, "cudaMalloc failed for autotuning");
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    cudaFree(zbuf);
+    return fail(MFG_ERR_CUDA, "cudaEventCreate failed");
+  }
+  int rc = MFG_OK;
+  for (auto& in : pl->inst) {
+    const TuneKey key = tune_key(in);
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        const TuneVal& v = it->second;
+        in.g.vec_blocks = v.vec_blocks;
+        in.g.aat_want = v.aat_want;
+        in.g.time_simt = v.time_simt;
+        in.g.fft_x = v.fft_x;
+        in.g.fft_y = v.fft_y;
+        in.tune_precond_us = v.precond_us;
+        in.tune_aat_us = v.aat_us;
+        in.tuned = 1;
+        in.measured = 0;
+        continue;
+      }
+    }
+    rc = tune_instance(in, zbuf, s, a, b);
+    if (rc != MFG_OK) break;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = TuneVal{in.g.vec_blocks, in.g.aat_want, in.g.time_simt, in.g.fft_x, in.g.fft_y,
+                                in.tune_precond_us, in.tune_aat_us};
+  }
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(zbuf);
+  drop_graph(pl);  // the next mfg_solve captures the new launch shapes
+  if (rc != MFG_OK) return rc;
+  CK(cudaGetLastError());
+  return MFG_OK;
+}
+
+int mfg_get_schedule(mfg_plan_t pl, int b, mfg_schedule* out) {
+  int rc = check_b(pl, b);
+  if (rc != MFG_OK) return rc;
+  if (!out) return fail(MFG_ERR_INVALID_ARG, "null output");
+  const Inst& in = pl->inst[b];
+  const Geom& g = in.g;
+  std::memset(out, 0, sizeof(*out));
+  out->tuned = in.tuned;
+  out->measured = in.measured;
+  const bool tc = in.p.precision == MFG_MIXED_TC && time_tc_supported(g.nt) && in.p.l != 0 && !g.time_simt;
+  out->time_pass = tc ? MFG_TIME_TENSOR_CORES : MFG_TIME_CUDA_CORES;
+  const int fy = g.fft_y && fft_supported(g.ny) && in.tabs.twy32 != nullptr;
+  const int fx = g.fft_x && g.nx > 1 && fft_supported(g.nx) && in.tabs.twx32 != nullptr;
+  if (in.p.dim == 1) {
+    out->fft[0] = fy;
+  } else {
+    out->fft[0] = fx;
+    out->fft[1] = fy;
+  }
+  out->aat_blocks = aat_blocks(g);
+  out->vec_blocks = g.vec_blocks;
+  out->precond_us = in.tune_precond_us;
+  out->aat_us = in.tune_aat_us;
+  return MFG_OK;
+}
+
 
 int mfg_set_fault_injection(mfg_plan_t pl, int what) {
   if (!pl) return fail(MFG_ERR_INVALID_ARG, "null plan");
@@ -359,7 +580,7 @@ int mfg_plan(const mfg_problem* probs, int batch, mfg_plan_t* out) {
     Inst& in = pl->inst[b];
     in.p = probs[b];
     in.g = make_geom(in.p);
-    in.cf = Coef{in.p.f_a, in.p.f_b, in.p.g_a, in.p.gamma};
+    in.cf = Coef{in.p.f_a, in.p.f_b, in.p.g_a, in.p.gamma, in.p.qprime};
     in.field_off = fo;
     in.primal_off = po;
     in.dual_off = dof;
@@ -370,7 +591,10 @@ int mfg_plan(const mfg_problem* probs, int batch, mfg_plan_t* out) {
     int rc = build_prec_tables(in.p, in.g, &in.tabs, &err);
     if (rc != MFG_OK) return bail(rc, err);
     const size_t n = (size_t)in.g.n;
-    size_t npart = (size_t)std::max<long long>(std::max(2 * kRedBlocks, aat_blocks(in.g)),
+    // partial sums for the largest grids any launch choice may use
+    Geom gmax = in.g;
+    gmax.aat_want = kAatWantMax;
+    size_t npart = (size_t)std::max<long long>(std::max(2 * kVecBlocksMax, aat_blocks(gmax)),
                                                fft_dot_partials(in.g));
     if (cudaMalloc(&in.r, n * 8) != cudaSuccess || cudaMalloc(&in.pv, n * 8) != cudaSuccess ||
         cudaMalloc(&in.q, n * 8) != cudaSuccess || cudaMalloc(&in.zp, n * 8) != cudaSuccess ||
@@ -542,6 +766,8 @@ int mfg_adjoint(mfg_plan_t pl, int b, const double* y, const double* z, const do
     return fail(MFG_ERR_INVALID_ARG, "null array or stats pointer");
   if (!(tol > 0.0) || max_iter < 1) return fail(MFG_ERR_INVALID_ARG, "tol > 0 and max_iter >= 1 required");
   Inst& in = pl->inst[b];
+  if (in.p.qprime != 2.0)
+    return fail(MFG_ERR_UNSUPPORTED, "the adjoint is built for the quadratic Hamiltonian (q' = 2) only");
   const Geom& g = in.g;
   const size_t n = (size_t)g.n;
   if (!in.adj_t) {
@@ -562,7 +788,7 @@ int mfg_adjoint(mfg_plan_t pl, int b, const double* y, const double* z, const do
   launch_apply_C(g, in.adj_t, in.r, 1.0, nullptr, in.partials, in.sc, 3, s);
   CK(cudaMemsetAsync(in.adj_eta, 0, n * 8, s));
   launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s);
-  launch_init_p(g.n, in.zp, in.pv, in.r, in.partials, in.sc, s);
+  launch_init_p(g.n, in.zp, in.pv, in.r, in.partials, in.sc, s, g.vec_blocks);
   long long launches = 3 + precond_kernel_count(g);
   DevScalars hs;
   for (;;) {
@@ -574,7 +800,7 @@ int mfg_adjoint(mfg_plan_t pl, int b, const double* y, const double* z, const do
     launch_ct_hinv(g, in.cf, y, in.pv, nullptr, in.adj_t, s, in.sc);
     launch_apply_C(g, in.adj_t, in.q, 1.0, nullptr, in.partials, in.sc, 2, s, in.pv);
     launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s, &dot, &zr);
-    launch_update_p(g.n, in.zp, in.pv, in.sc, 0, 0, s);
+    launch_update_p(g.n, in.zp, in.pv, in.sc, 0, 0, s, g.vec_blocks);
     launches += 3 + precond_step_kernel_count(g, in.tabs);
   }
   // mu = H^{-1}(g - C^T eta), then the contractions

@@ -13,6 +13,9 @@ constexpr int kThreads = 256;        // threads per block for 1-D launches
 // Fixed grid of the grid-stride reduction kernels.  Kept small: every thread
 // pays a warp-shuffle tree of FP64 adds at the end, and FP64 issue is scarce.
 constexpr int kRedBlocks = 152 * 2;
+constexpr int kVecBlocksMax = 152 * 4;   // largest vec_blocks the autotuner tries
+constexpr int kAatWantDefault = 152 * 8;
+constexpr int kAatWantMax = 152 * 16;    // largest aat_want the autotuner tries
 constexpr int kMaxNt = 256;          // largest N_t of the fused time-transform kernel
 
 // Geometry and coefficients of one instance on the device.  Internally every
@@ -29,12 +32,20 @@ struct Geom {
   double idx, idy;  // 1/dx, 1/dy
   double idt;       // 1/dt
   double nu;
+  // Launch choices: defaults from make_geom, replaced by mfg_autotune's
+  // measured ones.  They change launch shapes and pass variants, never the
+  // operator a kernel applies.
+  int vec_blocks;   // grid cap of the vector and reduction kernels
+  int aat_want;     // target block count of the AAt stencil launch
+  int time_simt;    // 1: time pass on the CUDA cores even where the tensor-core pass applies
+  int fft_x, fft_y; // 1: FFT spatial pass where the axis length allows it; 0: dense pass
 };
 
 // Coefficients of f_eff(m) = a m + b m^2 + c(x) (Sec. 2 calF).
 struct Coef {
   double f_a, f_b, g_a;  // g enters the last plane divided by dt
   double gamma;
+  double qprime;         // Hamiltonian exponent q' (eq. power_hamiltonian)
 };
 
 // Per-instance scalar state in device memory, written by the last block of the
@@ -64,10 +75,11 @@ int validate_problem(const mfg_problem& p, int idx);
 Geom make_geom(const mfg_problem& p);
 int set_error(int code, const std::string& msg);
 
-// Grid-stride 1-D launch shape shared by reduction kernels.
-inline int red_blocks(long long n) {
+// Grid-stride 1-D launch shape shared by reduction kernels: enough blocks
+// for one element per thread, at most `cap`.
+inline int red_blocks(long long n, int cap = kRedBlocks) {
   long long b = (n + kThreads - 1) / kThreads;
-  return (int)(b < kRedBlocks ? (b > 0 ? b : 1) : kRedBlocks);
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 // ---------------------------------------------------------------- kernels --
@@ -85,14 +97,15 @@ int aat_kernel_count(int df64);
 int aat_blocks(const Geom& g);
 
 // Vector kernels (k_cg.cu).
+// `cap`: grid cap (Geom::vec_blocks).
 void launch_init_p(long long n, const double* zp, double* p, const double* r, double* partials,
-                   DevScalars* sc, cudaStream_t s);
+                   DevScalars* sc, cudaStream_t s, int cap = kRedBlocks);
 void launch_update_zr(long long n, double* z, double* r, const double* p, const double* q,
-                      double* partials, DevScalars* sc, cudaStream_t s);
+                      double* partials, DevScalars* sc, cudaStream_t s, int cap = kRedBlocks);
 void launch_dot_beta(long long n, const double* r, const double* zp, const double* q, int flexible,
-                     double* partials, DevScalars* sc, cudaStream_t s);
+                     double* partials, DevScalars* sc, cudaStream_t s, int cap = kRedBlocks);
 void launch_update_p(long long n, const double* zp, double* p, DevScalars* sc,
-                     cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
+                     cudaGraphConditionalHandle h, int use_handle, cudaStream_t s, int cap = kRedBlocks);
 void launch_scalars_begin(DevScalars* sc, cudaGraphConditionalHandle h, int use_handle,
                           cudaStream_t s);
 

@@ -56,7 +56,8 @@ def test_plan_rejects_invalid_problems_without_gpu():
     import mfg_inputs as mi
     L = _lib()
     base = mi.small(1)["problem"]
-    for bad, code in ((dict(base, qprime=1.5), L.MFG_ERR_UNSUPPORTED), (dict(base, nt=1), L.MFG_ERR_INVALID_ARG),
+    for bad, code in ((dict(base, qprime=1.0), L.MFG_ERR_UNSUPPORTED), (dict(base, qprime=25.0), L.MFG_ERR_UNSUPPORTED),
+                      (dict(base, nt=1), L.MFG_ERR_INVALID_ARG),
                       (dict(base, nu=-1.0), L.MFG_ERR_INVALID_ARG), (dict(base, l=3), L.MFG_ERR_INVALID_ARG),
                       (dict(base, f_a=-0.1), L.MFG_ERR_INVALID_ARG), (dict(base, nt=300), L.MFG_ERR_UNSUPPORTED)):
         with pytest.raises(L.MfgError) as e:

@@ -326,3 +326,41 @@ def test_prox_step_matches_oracle(case):
     assert rel(host(y), ref) <= 1e-12
     assert np.abs(host(y) - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
     assert rel(host(ybar), ref_bar) <= 1e-12
+
+
+@pytest.mark.parametrize("qp", [1.5, 3.0])
+@pytest.mark.parametrize("case", CASES[:2] + CASES[4:5])
+def test_prox_general_hamiltonian(case, qp):
+    """prox for H = |p|^{q'}/q' (b_hat = |w|^q/(q m^{q-1}), Sec. 2) against the
+    oracle's nested bisection."""
+    import torch
+    inst = _inst(case)
+    p = dict(inst["problem"], qprime=qp)
+    plan = _plan(p)
+    s, n, c = ops.sizes(p)
+    v = mi.random_field((c, p["nt"]) + tuple(p["n"]), 91, -2.0, 2.0)
+    v[0] += 0.5
+    y = torch.empty(c * n, dtype=torch.float64, device="cuda")
+    for tau in (0.05, 1.0):
+        lib().mfg_prox(plan, 0, tau, dev(v), dev(inst["V"]), dev(inst["W"]), y)
+        torch.cuda.synchronize()
+        ref = oracle_prox(p, tau, v, inst["V"], inst["W"]).reshape(-1)
+        got = host(y)
+        assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+        assert np.all(got[:n] >= 0)
+
+
+@pytest.mark.parametrize("qp", [1.5, 3.0])
+@pytest.mark.parametrize("precision", ["fp64", "mixed_tc"])
+def test_cp_iterate_general_hamiltonian(qp, precision):
+    """The CP iterate with the general power Hamiltonian against the oracle."""
+    inst = _inst(CASES[1])
+    iters = 10
+    rc, st, y, ybar, z = _gpu_cp(inst, iters, precision, cg_tol=1e-12, qprime=qp)
+    assert rc == 0 and st.status == 0 and st.cp_iters == iters
+    p = dict(inst["problem"], qprime=qp)
+    ref = Solver(p, inst["m0"], inst["V"], inst["W"], method="modal").run(inst["y0"], iters=iters)
+    err = rel(y, ref["y"])
+    print(f"\nq' = {qp}, {precision}: rel err {err:.2e}")
+    assert err <= cp_bound(p)
+    assert rel(ybar, ref["ybar"]) <= cp_bound(p)

@@ -3,6 +3,7 @@ the shapes and parameters their docstrings state, densities are normalised on
 the grid (sum m0 dx^d = 1), fields are reproducible from their seeds, and the
 uneven batch draws its parameters from the stated sets."""
 import numpy as np
+import pytest
 
 import mfg_inputs as mi
 
@@ -75,3 +76,25 @@ def test_initial_iterate_layout():
     assert y0.shape == (5, 4, 7, 5)
     assert np.array_equal(y0[0], np.broadcast_to(inst["m0"], (4, 7, 5)))
     assert not y0[1:].any()
+
+
+def test_paper_problems():
+    """Problem 1 (Sec. 5.1) and Problem 2 (Sec. 5.2) as the paper states them."""
+    p1 = mi.problem1(N=16)
+    p = p1["problem"]
+    assert p["n"] == (16, 16) and p["nt"] == 128 and p["bc"] == ("periodic", "periodic")
+    assert p["f_a"] == 0.0 and p["f_b"] == 0.5 and p["gamma"] == 5e-4 and p["cg_rule"] == 1
+    X, Y = mi.nodes(p)
+    np.testing.assert_allclose(p1["V"], -0.5 * (np.sin(2 * np.pi * Y) + np.sin(2 * np.pi * X) + np.cos(4 * np.pi * X)))
+    assert np.all(p1["m0"] == 1.0) and np.all(p1["W"] == 0.0)
+    assert p["cp_tol"] == pytest.approx(1e-4 * 16.0)
+    p2 = mi.problem2(N=16)
+    q = p2["problem"]
+    assert q["bc"] == ("neumann", "neumann") and q["nt"] == 128 and q["gamma"] == 5e-3
+    assert q["f_a"] == 0.0 and q["f_b"] == 0.0 and q["g_a"] == pytest.approx(1e3)
+    X, Y = mi.nodes(q)
+    x, y = X - 0.5, Y - 0.5
+    assert x.min() == pytest.approx(-0.5 + 1.0 / 17) and x.max() == pytest.approx(0.5 - 1.0 / 17)
+    np.testing.assert_allclose(p2["m0"], 3 * np.exp(-128 * ((x + 0.25) ** 2 + (y - 0.25) ** 2)))
+    np.testing.assert_allclose(p2["W"], -1e3 * 3 * np.exp(-128 * ((x - 0.25) ** 2 + (y + 0.25) ** 2)))
+    assert np.all(p2["V"] == 0.0)

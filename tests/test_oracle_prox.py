@@ -135,3 +135,59 @@ def test_c_bisection_equals_numpy_bisection(dim, f_b):
         r_c = prox_cells(tau, v, a, f_b, c)
         assert np.array_equal(r_np, r_c, equal_nan=True)
         assert (r_c[0] == 0).any() and (r_c[0] > 0).any()
+
+
+def _cell_objective_q(u, qp, mbar, wbar, tau, a, b, c):
+    m, w = u[0], u[1:]
+    if m <= 0:
+        return np.inf
+    q = qp / (qp - 1.0)
+    F = 0.5 * a * m * m + b * m ** 3 / 3 + c * m
+    return np.linalg.norm(w) ** q / (q * m ** (q - 1)) + F + ((m - mbar) ** 2 + (w - wbar) @ (w - wbar)) / (2 * tau)
+
+
+@pytest.mark.parametrize("qp", [1.5, 3.0])
+def test_general_q_prox_matches_brute_force(qp):
+    """The prox for H = |p|^{q'}/q' against direct minimisation of its definition
+    (b_hat = |w|^q/(q m^{q-1}) of Sec. 2 plus F, plus the proximal term)."""
+    from oracle.prox import prox_cells_q
+    rng = np.random.default_rng(int(qp * 10))
+    for trial in range(12):
+        ncomp = 4 if trial % 2 == 0 else 2
+        mbar = rng.uniform(0.2, 2.0)
+        wbar = rng.uniform(-1.5, 1.5, size=ncomp)
+        tau, a, b, c = rng.uniform(0.1, 1.5), rng.uniform(0.2, 2.0), rng.uniform(0.0, 0.5), rng.normal(0.0, 0.3)
+        v = np.concatenate([[mbar], wbar])[:, None]
+        got = prox_cells_q(qp, tau, v, np.array([a]), b, np.array([c]))[:, 0]
+        bounds = [(1e-12, None)] + [((0, None) if i % 2 == 0 else (None, 0)) for i in range(ncomp)]
+        best = None
+        for m_init in (1e-2, 0.3, 1.0, 2.0):
+            x0 = np.concatenate([[m_init], project_K(wbar) * 0.5])
+            r = minimize(_cell_objective_q, x0, args=(qp, mbar, wbar, tau, a, b, c), method="L-BFGS-B",
+                         bounds=bounds, options={"ftol": 1e-15, "gtol": 1e-12, "maxiter": 20000})
+            if best is None or r.fun < best.fun:
+                best = r
+        f_got = _cell_objective_q(got, qp, mbar, wbar, tau, a, b, c) if got[0] > 0 else np.inf
+        assert f_got <= best.fun + 1e-9 * max(1.0, abs(best.fun))
+        assert np.abs(got - best.x).max() <= 2e-5 * max(1.0, np.abs(best.x).max())
+
+
+def test_general_q_prox_reduces_to_quadratic():
+    """At q' = 2 the nested-bisection solver gives the q' = 2 prox; the zero
+    branch and P = 0 (w = 0, m from m - m_bar + tau f(m) = 0) hold for any q'."""
+    from oracle.prox import prox_cells_numpy, prox_cells_q
+    rng = np.random.default_rng(5)
+    v = rng.uniform(-2.0, 2.0, size=(5, 400))
+    v[0] += 0.5
+    a = rng.uniform(0.0, 2.0, size=400)
+    c = rng.normal(size=400)
+    ref = prox_cells_numpy(0.7, v, a, 0.3, c)
+    got = prox_cells_q(2.0, 0.7, v, a, 0.3, c)
+    assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+    for qp in (1.5, 3.0):
+        w0 = v.copy()
+        w0[1::2] = -np.abs(w0[1::2])  # P = 0: every flux outside the cone
+        w0[2::2] = np.abs(w0[2::2])
+        out = prox_cells_q(qp, 0.7, w0, a, 0.0, c)
+        m_lin = np.maximum(0.0, (w0[0] - 0.7 * c) / (1.0 + 0.7 * a))
+        assert np.abs(out[0] - m_lin).max() <= 1e-12 and np.all(out[1:] == 0.0)
