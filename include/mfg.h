@@ -69,8 +69,10 @@ enum { MFG_CG_FIXED = 0, MFG_CG_ADAPTIVE = 1 };
 /* What the PCG tolerance is relative to (the paper does not say, Sec. 5).
  * MFG_CG_REF_RHS: ||b||_2 of the system solved in eq. CC*,
  *   AAt z = C (x_l + sigma ybar_l) - sigma d, i.e. stop when
- *   ||b - AAt z|| <= tol ||b|| (the usual CG convention; one extra AAt apply
- *   per CP iteration forms ||b|| = ||AAt z_l + sigma (C ybar_l - d)||).
+ *   ||b - AAt z|| <= tol ||b|| (the usual CG convention).  b = AAt z_l +
+ *   sigma (C ybar_l - d): the plan keeps AAt z in an n-double vector, applied
+ *   once per mfg_solve call to the caller's z and then carried by the CP loop
+ *   (AAt z_{l+1} = b - r_final, r_final the recursive PCG residual).
  * MFG_CG_REF_RESID: the 2-norm of the residual of the warm start z_l,
  *   sigma (C ybar_l - d): a stricter stop that does not loosen as z_l grows. */
 enum { MFG_CG_REF_RHS = 0, MFG_CG_REF_RESID = 1 };

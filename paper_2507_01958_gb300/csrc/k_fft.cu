@@ -94,7 +94,9 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
   // takes its elements in batches whose loads are all issued before any of
   // them is used or stored, so one memory latency covers a batch.
   constexpr int PER = (LB * N + 255) / 256;        // elements per thread
-  constexpr int BL = ZR ? (PER < 4 ? PER : 4) : (PER < 8 ? PER : 8);
+  // (FP32 input: all of a thread's loads at once for N <= 512; the fused PCG
+  // update moves four FP64 operands per element, so it takes 4 at a time)
+  constexpr int BL = ZR ? (PER < 4 ? PER : 4) : (PER < 32 ? PER : 32);
   auto element = [&](int idx, int& l, int& i, long long& addr) -> bool {
     if (CONTIG) { l = idx / N; i = idx % N; } else { i = idx / LB; l = idx % LB; }
     const long long line = line0 + l;
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
     cx<T>* dst = buf1 + q * NP;
     int Ns = 1;
     for (int st = 0; st < n4; ++st, Ns <<= 2) {
+#pragma unroll
       for (int j = lane; j < N / 4; j += 32) {
         const int k = j & (Ns - 1);
         const int m = k * (N / (4 * Ns));
@@ -212,6 +215,7 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
       cx<T>* t = src; src = dst; dst = t;
     }
     if (n2) {
+#pragma unroll
       for (int j = lane; j < N / 2; j += 32) {
         const int k = j & (Ns - 1);
         const cx<T> a = src[swz(j)];
@@ -257,7 +261,7 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
   // ---- store (with the fused dot products of the PCG step when DOT; a
   // batch's dot operands are loaded before its stores)
   double a0 = 0.0, a1 = 0.0;
-  constexpr int BS = PER < 8 ? PER : 8;
+  constexpr int BS = DOT ? (PER < 8 ? PER : 8) : (PER < 16 ? PER : 16);
 #pragma unroll 1
   for (int b0 = 0; b0 < PER; b0 += BS) {
     int ls[BS], is[BS];

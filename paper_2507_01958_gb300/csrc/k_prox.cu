@@ -255,7 +255,8 @@ __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const dou
                                                       const double* __restrict__ V,
                                                       const double* __restrict__ W, double* partials,
                                                       DevScalars* sc, cudaGraphConditionalHandle h,
-                                                      int use_handle) {
+                                                      int use_handle, double* __restrict__ Az,
+                                                      const double* __restrict__ rfin) {
   constexpr int NW = ACTX ? 4 : 2;
   const long long n = g.n;
   const double tau = sc->tau, theta = sc->theta;
@@ -276,6 +277,7 @@ __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const dou
     const int jm = j == 0 ? (g.pery ? g.ny - 1 : 0) : j - 1;
     const int jp = j == g.ny - 1 ? (g.pery ? 0 : g.ny - 1) : j + 1;
     const double zc = z[e];
+    if (Az != nullptr) Az[e] -= rfin[e];  // AAt z_{l+1} = b - r_final (stop reference)
     const double dyp = zc - z[rowi + jp], dym = z[rowi + jm] - zc;
     double Kz = g.ay * (dyp - dym);
     double d[NW];
@@ -382,19 +384,20 @@ __global__ void __launch_bounds__(kThreads) k_prox_plain(Geom g, Coef cf, double
 
 void launch_prox_cp(const Geom& g, const Coef& cf, const double* z, double* y, double* ybar,
                     const double* V, const double* W, double* partials, DevScalars* sc,
-                    cudaGraphConditionalHandle h, int use_handle, cudaStream_t s) {
+                    cudaGraphConditionalHandle h, int use_handle, cudaStream_t s, double* Az,
+                    const double* rfin) {
   const int nb = red_blocks(g.n, g.vec_blocks);
   // the general-q' root finder is its own instantiation, so the q' = 2 kernel
   // keeps its registers
   if (cf.qprime != 2.0) {
     if (g.actx)
-      k_prox_cp<1, true><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle);
+      k_prox_cp<1, true><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle, Az, rfin);
     else
-      k_prox_cp<0, true><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle);
+      k_prox_cp<0, true><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle, Az, rfin);
   } else if (g.actx) {
-    k_prox_cp<1, false><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle);
+    k_prox_cp<1, false><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle, Az, rfin);
   } else {
-    k_prox_cp<0, false><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle);
+    k_prox_cp<0, false><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle, Az, rfin);
   }
 }
 

@@ -47,6 +47,11 @@ __device__ __forceinline__ int wrap_or_neg(int i, int N, int per) {
 // mode 0: r = alpha * (C v - d), d = m0/dt on plane 0 when m0 != nullptr.
 // mode 1: CP right-hand side r = sigma (C v - d) with sigma from the device
 //         scalars; reduces ||r||^2, resets the PCG state for the new solve.
+//         With Az != nullptr (the MFG_CG_REF_RHS stop reference) Az holds
+//         AAt z_l on entry and b = AAt z_l + r, the right-hand side of the
+//         system of eq. CC*, on exit; ||b||^2 becomes the reference of the
+//         relative tolerance, and a warm start already inside it stops the
+//         solve before its first iteration.
 // mode 2: PCG step of the adjoint Schur system: r = C v, reduces pdot.r,
 //         alpha = rz/(pdot.r).
 // mode 3: adjoint right-hand side r = C v; reduces ||r||^2, resets the PCG
@@ -56,7 +61,8 @@ __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __re
                                                       double* __restrict__ r, double alpha,
                                                       const double* __restrict__ m0,
                                                       const double* __restrict__ pdot,
-                                                      double* partials, DevScalars* sc, int mode) {
+                                                      double* partials, DevScalars* sc, int mode,
+                                                      double* __restrict__ Az) {
   if (mode == 2 && sc->cg_done) return;
   if (mode == 1) alpha = sc->sigma;
   const long long n = g.n;
@@ -69,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __re
   const double anu = alpha * g.nu, ax = ACTX ? g.ax : 0.0;
   const double kc = anu * 2.0 * (ax + g.ay), kx = anu * ax, ky = anu * g.ay;
   const double aix = alpha * g.idx, aiy = alpha * g.idy, aidt = alpha * g.idt;
-  double acc = 0.0;
+  double acc = 0.0, accb = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(e % g.ny);
@@ -100,13 +106,18 @@ __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __re
     val = fma(aidt, mc - mprev, val);
     r[e] = val;
     acc = (mode == 2) ? fma(pdot[e], val, acc) : fma(val, val, acc);
+    if (Az != nullptr) {
+      const double b = Az[e] + val;
+      Az[e] = b;
+      accb = fma(b, b, accb);
+    }
   }
   if (mode == 0) return;
-  double part[1] = {acc};
-  block_sum<1>(part);
-  if (!publish_and_check_last<1>(part, partials, &sc->counter)) return;
-  double tot[1];
-  gather_partials<1>(partials, tot);
+  double part[2] = {acc, accb};
+  block_sum<2>(part);
+  if (!publish_and_check_last<2>(part, partials, &sc->counter)) return;
+  double tot[2];
+  gather_partials<2>(partials, tot);
   if (mode == 2) {
     if (flat_tid() == 0) {
       sc->pq = tot[0];
@@ -122,15 +133,17 @@ __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __re
     return;
   }
   if (flat_tid() == 0) {
-    sc->bnorm2 = tot[0];
-    sc->rr = tot[0];  // ||r_0||^2; the MFG_CG_REF_RHS pass replaces bnorm2 by ||b||^2
+    const double rr0 = tot[0], b2 = (Az != nullptr) ? tot[1] : tot[0];
+    sc->bnorm2 = b2;  // reference of the relative tolerance: ||b||^2 or ||r_0||^2
+    sc->rr = rr0;
     sc->cg_it = 0;
     // The paper's adaptive rule, min{1e-4, max{1e-6, 1e-4 r}} (Sec. 5).
     double tol = sc->cg_tol_fixed;
     if (sc->cg_rule == MFG_CG_ADAPTIVE) tol = fmin(1e-4, fmax(1e-6, 1e-4 * sc->r_last));
     sc->cg_tol = tol;
-    sc->cg_done = !(tot[0] > 0.0);  // also true for NaN: flagged below
-    if (!isfinite(tot[0])) {
+    // no iteration when r_0 = 0 or r_0 is already inside the tolerance (NaN: flagged below)
+    sc->cg_done = !(rr0 > 0.0) || rr0 <= tol * tol * b2;
+    if (!isfinite(rr0) || !isfinite(b2)) {
       sc->cg_done = 1;
       sc->status = MFG_ERR_NONFINITE;
     }
@@ -139,12 +152,13 @@ __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __re
 }
 
 void launch_apply_C(const Geom& g, const double* v, double* r, double alpha, const double* m0,
-                    double* partials, DevScalars* sc, int mode, cudaStream_t s, const double* pdot) {
+                    double* partials, DevScalars* sc, int mode, cudaStream_t s, const double* pdot,
+                    double* Az) {
   const int nb = red_blocks(g.n, g.vec_blocks);
   if (g.actx)
-    k_apply_C<1><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, pdot, partials, sc, mode);
+    k_apply_C<1><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, pdot, partials, sc, mode, Az);
   else
-    k_apply_C<0><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, pdot, partials, sc, mode);
+    k_apply_C<0><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, pdot, partials, sc, mode, Az);
 }
 
 // ----------------------------------------------------------------- C^T p --
@@ -253,19 +267,6 @@ __device__ __forceinline__ Cols aat_cols(const Geom& g, int i, int j) {
   return c;
 }
 
-// Last block of a mode-2 pass: ||b||^2 becomes the reference of the relative
-// PCG tolerance; a warm start already inside it needs no PCG iteration.
-__device__ __forceinline__ void stop_reference(DevScalars* sc, double b2) {
-  sc->bnorm2 = b2;
-  if (!isfinite(b2)) {
-    sc->cg_done = 1;
-    if (sc->status == MFG_OK) sc->status = MFG_ERR_NONFINITE;
-  } else if (sc->rr <= sc->cg_tol * sc->cg_tol * b2) {
-    sc->cg_done = 1;
-  }
-  sc->counter = 0;
-}
-
 template <int ACTX>
 __global__ void __launch_bounds__(AJ * AI) k_aat_x(Geom g, AatCoef a, int kc, const double* __restrict__ p,
                                                    double* __restrict__ X, double* __restrict__ KP,
@@ -291,17 +292,13 @@ __global__ void __launch_bounds__(AJ * AI) k_aat_x(Geom g, AatCoef a, int kc, co
 }
 
 // mode 0: q = AAt p.  mode 1 (PCG step): also reduces p.q and sets
-// alpha = rz/(p.q) in the device scalars.  mode 2 (stop reference of
-// MFG_CG_REF_RHS, once per CP iteration with p = z_l): reduces
-// ||AAt z_l + r0||^2 = ||b||^2 with r0 = `r2`, stores it as the reference of
-// the relative tolerance and stops the solve at once if ||r0|| <= tol ||b||;
-// q is not stored.
+// alpha = rz/(p.q) in the device scalars.
 template <int ACTX>
 // 2-D: capped at 64 registers (four 256-thread blocks per SM) to hide the load latency
 __global__ void __launch_bounds__(AJ * AI, ACTX ? 4 : 3) k_aat_q(Geom g, AatCoef a, int kc, const double* __restrict__ X,
                                                    const double* __restrict__ KP, const double* __restrict__ p,
                                                    double* __restrict__ q, double* partials, DevScalars* sc,
-                                                   int mode, const double* __restrict__ r2) {
+                                                   int mode) {
   if (mode != 0 && sc->cg_done) return;
   const int j = blockIdx.x * AJ + threadIdx.x, i = blockIdx.y * AI + threadIdx.y;
   double acc = 0.0;
@@ -318,13 +315,8 @@ __global__ void __launch_bounds__(AJ * AI, ACTX ? 4 : 3) k_aat_q(Geom g, AatCoef
       t = fma(a.idt2, xprev, t);
       t = fma(-2.0, KP[base + row + j], t);
       const double qv = fma(a.c4, xc, -t);
-      if (mode == 2) {
-        const double bv = qv + r2[base + row + j];
-        acc = fma(bv, bv, acc);
-      } else {
-        q[base + row + j] = qv;
-        if (mode == 1) acc = fma(qv, p[base + row + j], acc);
-      }
+      q[base + row + j] = qv;
+      if (mode == 1) acc = fma(qv, p[base + row + j], acc);
       xprev = xc;
       base += g.S;
     }
@@ -335,10 +327,6 @@ __global__ void __launch_bounds__(AJ * AI, ACTX ? 4 : 3) k_aat_q(Geom g, AatCoef
   if (!publish_and_check_last<1>(part, partials, &sc->counter)) return;
   double tot[1];
   gather_partials<1>(partials, tot);
-  if (mode == 2) {
-    if (flat_tid() == 0) stop_reference(sc, tot[0]);
-    return;
-  }
   if (flat_tid() == 0) {
     sc->pq = tot[0];
     if (tot[0] > 0.0 && isfinite(tot[0])) {
@@ -397,7 +385,7 @@ template <int ACTX>
 __global__ void __launch_bounds__(AJ * AI) k_aat_q_df(Geom g, AatCoef ad, int kc, const df* __restrict__ X,
                                                       const df* __restrict__ KP, const double* __restrict__ p,
                                                       double* __restrict__ q, double* partials, DevScalars* sc,
-                                                      int mode, const double* __restrict__ r2) {
+                                                      int mode) {
   if (mode != 0 && sc->cg_done) return;
   const int j = blockIdx.x * AJ + threadIdx.x, i = blockIdx.y * AI + threadIdx.y;
   double acc = 0.0;
@@ -417,13 +405,8 @@ __global__ void __launch_bounds__(AJ * AI) k_aat_q_df(Geom g, AatCoef ad, int kc
       t = df_add(t, df_mul(idt2, xprev));
       t = df_sub(t, df_scale2(KP[base + row + j]));
       const double qv = df_to_double(df_sub(df_mul(c4, xc), t));
-      if (mode == 2) {
-        const double bv = qv + r2[base + row + j];
-        acc = fma(bv, bv, acc);
-      } else {
-        q[base + row + j] = qv;
-        if (mode == 1) acc = fma(qv, p[base + row + j], acc);
-      }
+      q[base + row + j] = qv;
+      if (mode == 1) acc = fma(qv, p[base + row + j], acc);
       xprev = xc;
       base += g.S;
     }
@@ -434,10 +417,6 @@ __global__ void __launch_bounds__(AJ * AI) k_aat_q_df(Geom g, AatCoef ad, int kc
   if (!publish_and_check_last<1>(part, partials, &sc->counter)) return;
   double tot[1];
   gather_partials<1>(partials, tot);
-  if (mode == 2) {
-    if (flat_tid() == 0) stop_reference(sc, tot[0]);
-    return;
-  }
   if (flat_tid() == 0) {
     sc->pq = tot[0];
     if (tot[0] > 0.0 && isfinite(tot[0])) {
@@ -452,7 +431,7 @@ __global__ void __launch_bounds__(AJ * AI) k_aat_q_df(Geom g, AatCoef ad, int kc
 }
 
 void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, double* partials,
-                DevScalars* sc, int mode, cudaStream_t s, int df64, const double* r2) {
+                DevScalars* sc, int mode, cudaStream_t s, int df64) {
   const AatCoef a = aat_coef(g);
   const int kc = aat2_chunk(g);
   const dim3 grid = aat2_grid(g, kc), block(AJ, AI);
@@ -461,10 +440,10 @@ void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, doub
     df* KP = X + g.n;
     if (g.actx) {
       k_aat_x_df<1><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
-      k_aat_q_df<1><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode, r2);
+      k_aat_q_df<1><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
     } else {
       k_aat_x_df<0><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
-      k_aat_q_df<0><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode, r2);
+      k_aat_q_df<0><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
     }
     return;
   }
@@ -472,10 +451,10 @@ void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, doub
   double* KP = scratch + g.n;
   if (g.actx) {
     k_aat_x<1><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
-    k_aat_q<1><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode, r2);
+    k_aat_q<1><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
   } else {
     k_aat_x<0><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
-    k_aat_q<0><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode, r2);
+    k_aat_q<0><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
   }
 }
 

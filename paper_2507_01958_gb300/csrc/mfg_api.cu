@@ -58,6 +58,7 @@ struct Inst {
   double* partials = nullptr;
   DevScalars* sc = nullptr;  // points into the plan's contiguous array
   double *adj_t = nullptr, *adj_eta = nullptr;  // adjoint workspace, allocated on first use
+  double* Az = nullptr;  // MFG_CG_REF_RHS: AAt z, carried across CP iterations (stop reference)
   int tuned = 0, measured = 0;                  // launch choices from mfg_autotune
   double tune_precond_us = 0.0, tune_aat_us = 0.0;
 };
@@ -167,10 +168,10 @@ namespace {
 
 void free_inst(Inst& in) {
   free_prec_tables(&in.tabs);
-  void* ptrs[] = {in.r, in.pv, in.q, in.zp, in.work64, in.work32, in.partials, in.adj_t, in.adj_eta};
+  void* ptrs[] = {in.r, in.pv, in.q, in.zp, in.work64, in.work32, in.partials, in.adj_t, in.adj_eta, in.Az};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  in.r = in.pv = in.q = in.zp = in.work64 = in.partials = in.adj_t = in.adj_eta = nullptr;
+  in.r = in.pv = in.q = in.zp = in.work64 = in.partials = in.adj_t = in.adj_eta = in.Az = nullptr;
   in.work32 = nullptr;
 }
 
@@ -188,18 +189,20 @@ int check_b(mfg_plan_t pl, int b) {
   return MFG_OK;
 }
 
-// kernels per CP iteration outside PCG (rhs, [stop reference], precond, init_p, arm, prox)
-// and per PCG iteration
-int launches_cp(const Inst& in) {
-  return 4 + precond_kernel_count(in.g) +
-         (in.p.cg_ref == MFG_CG_REF_RHS ? aat_kernel_count(in.p.precision == MFG_MIXED_DF) : 0);
-}
+// kernels per CP iteration outside PCG (rhs, precond, init_p, arm, prox), per
+// PCG iteration, and once per solve (the AAt z of the MFG_CG_REF_RHS reference)
+int launches_cp(const Inst& in) { return 4 + precond_kernel_count(in.g); }
+int launches_solve(const Inst& in) { return in.Az ? aat_kernel_count(in.p.precision == MFG_MIXED_DF) : 0; }
 
-// ||b|| of the system of eq. CC* as the PCG stop reference (MFG_CG_REF_RHS):
-// one AAt apply of the warm start z_l, added to r_0 = sigma (C ybar - d).
-void launch_stop_reference(const Inst& in, const double* z, cudaStream_t s) {
-  if (in.p.cg_ref != MFG_CG_REF_RHS) return;
-  launch_AAt(in.g, z, in.q, in.work64, in.partials, in.sc, 2, s, in.p.precision == MFG_MIXED_DF, in.r);
+// Stop reference of MFG_CG_REF_RHS, ||b|| of the system of eq. CC*: the
+// right-hand side b = AAt z_l + sigma (C ybar - d) needs AAt z_l.  It is
+// applied once per solve to the caller's z; afterwards the CP loop carries it:
+// the rhs kernel turns Az into b, the prox kernel subtracts the final PCG
+// residual (AAt z_{l+1} = b - r_final, up to the recursive residual's
+// rounding).
+void launch_stop_reference_start(const Inst& in, const double* z, cudaStream_t s) {
+  if (!in.Az) return;
+  launch_AAt(in.g, z, in.Az, in.work64, in.partials, in.sc, 0, s, in.p.precision == MFG_MIXED_DF);
 }
 int launches_cg(const Inst& in) {
   return 1 + aat_kernel_count(in.p.precision == MFG_MIXED_DF) + precond_step_kernel_count(in.g, in.tabs);
@@ -208,6 +211,20 @@ int launches_cg(const Inst& in) {
 // Captures the per-instance CP loop into `top` as a while-node branch.
 int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, const double* V,
                  const double* W, double* y, double* ybar, double* z) {
+  // prologue: AAt z of the stop reference, before the CP loop
+  std::vector<cudaGraphNode_t> pro;
+  if (in.Az) {
+    cudaStream_t s0 = pl->cap0;
+    CK(cudaStreamBeginCaptureToGraph(s0, top, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    launch_stop_reference_start(in, z, s0);
+    cudaStreamCaptureStatus cst0;
+    const cudaGraphNode_t* d0 = nullptr;
+    size_t n0 = 0;
+    CK(cudaStreamGetCaptureInfo(s0, &cst0, nullptr, nullptr, &d0, nullptr, &n0));
+    pro.assign(d0, d0 + n0);
+    cudaGraph_t tg = top;
+    CK(cudaStreamEndCapture(s0, &tg));
+  }
   cudaGraphConditionalHandle hc, hg;
   CK(cudaGraphConditionalHandleCreate(&hc, top, in.p.max_cp > 0 ? 1u : 0u, cudaGraphCondAssignDefault));
   cudaGraphNodeParams cp{};
@@ -216,7 +233,7 @@ int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, con
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t wcp;
-  CK(cudaGraphAddNode(&wcp, top, nullptr, nullptr, 0, &cp));
+  CK(cudaGraphAddNode(&wcp, top, pro.empty() ? nullptr : pro.data(), nullptr, pro.size(), &cp));
   cudaGraph_t body_cp = cp.conditional.phGraph_out[0];
   CK(cudaGraphConditionalHandleCreate(&hg, body_cp, 0, 0));
 
@@ -225,8 +242,7 @@ int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, con
   const int dfa = in.p.precision == MFG_MIXED_DF;
   cudaStream_t s = pl->cap0;
   CK(cudaStreamBeginCaptureToGraph(s, body_cp, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  launch_apply_C(g, ybar, in.r, 1.0, m0, in.partials, in.sc, 1, s);
-  launch_stop_reference(in, z, s);
+  launch_apply_C(g, ybar, in.r, 1.0, m0, in.partials, in.sc, 1, s, nullptr, in.Az);
   launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s);
   launch_init_p(g.n, in.zp, in.pv, in.r, in.partials, in.sc, s, g.vec_blocks);
   launch_scalars_begin(in.sc, hg, 1, s);
@@ -243,7 +259,7 @@ int add_instance(mfg_plan_t pl, Inst& in, cudaGraph_t top, const double* m0, con
   CK(cudaGraphAddNode(&wcg, body_cp, deps, nullptr, ndeps, &cg));
   cudaGraph_t body_cg = cg.conditional.phGraph_out[0];
   CK(cudaStreamUpdateCaptureDependencies(s, &wcg, nullptr, 1, cudaStreamSetCaptureDependencies));
-  launch_prox_cp(g, in.cf, z, y, ybar, V, W, in.partials, in.sc, hc, 1, s);
+  launch_prox_cp(g, in.cf, z, y, ybar, V, W, in.partials, in.sc, hc, 1, s, in.Az, in.r);
   CK(cudaStreamEndCapture(s, &body_cp));
 
   cudaStream_t s2 = pl->cap1;
@@ -295,9 +311,12 @@ int solve_eager(mfg_plan_t pl, const double* m0, const double* V, const double* 
     double* yb = y + in.primal_off;
     double* ybb = ybar + in.primal_off;
     double* zb = z + in.dual_off;
+    if (in.p.max_cp > 0) {
+      launch_stop_reference_start(in, zb, s);
+      pl->launches += launches_solve(in);
+    }
     for (int it = 0; it < in.p.max_cp; ++it) {
-      launch_apply_C(g, ybb, in.r, 1.0, m0b, in.partials, in.sc, 1, s);
-      launch_stop_reference(in, zb, s);
+      launch_apply_C(g, ybb, in.r, 1.0, m0b, in.partials, in.sc, 1, s, nullptr, in.Az);
       launch_precond(g, in.tabs, in.p.precision, in.r, in.zp, in.work64, in.work32, in.sc, s);
       launch_init_p(g.n, in.zp, in.pv, in.r, in.partials, in.sc, s, g.vec_blocks);
       pl->launches += launches_cp(in) - 2;  // the prox is counted below; nothing arms a graph node
@@ -312,7 +331,7 @@ int solve_eager(mfg_plan_t pl, const double* m0, const double* V, const double* 
         launch_update_p(g.n, in.zp, in.pv, in.sc, 0, 0, s, g.vec_blocks);
         pl->launches += launches_cg(in);
       }
-      launch_prox_cp(g, in.cf, zb, yb, ybb, Vb, Wb, in.partials, in.sc, 0, 0, s);
+      launch_prox_cp(g, in.cf, zb, yb, ybb, Vb, Wb, in.partials, in.sc, 0, 0, s, in.Az, in.r);
       pl->launches += 1;
       CK(cudaMemcpyAsync(&hs, in.sc, sizeof(hs), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
@@ -606,6 +625,8 @@ int mfg_plan(const mfg_problem* probs, int batch, mfg_plan_t* out) {
     }
     if (cudaMalloc(&in.work64, 2 * n * 8) != cudaSuccess)
       return bail(MFG_ERR_CUDA, "cudaMalloc failed for FP64 workspace");
+    if (in.p.cg_ref == MFG_CG_REF_RHS && cudaMalloc(&in.Az, n * 8) != cudaSuccess)
+      return bail(MFG_ERR_CUDA, "cudaMalloc failed for the stop-reference vector");
   }
   pl->field_total = fo;
   pl->primal_total = po;
@@ -721,7 +742,8 @@ int mfg_solve(mfg_plan_t pl, const double* m0, const double* V, const double* W,
     st[b].tau = h.tau;
     st[b].sigma = h.sigma;
     if (!eager)
-      pl->launches += (long long)launches_cp(pl->inst[b]) * h.cp_iters + (long long)launches_cg(pl->inst[b]) * h.cg_total;
+      pl->launches += (long long)launches_cp(pl->inst[b]) * h.cp_iters + (long long)launches_cg(pl->inst[b]) * h.cg_total +
+                      (pl->inst[b].p.max_cp > 0 ? launches_solve(pl->inst[b]) : 0);
     if (first == MFG_OK && h.status != MFG_OK) first = h.status;
   }
   if (first != MFG_OK) return fail(first, "an instance finished with a non-OK status");

@@ -84,15 +84,15 @@ inline int red_blocks(long long n, int cap = kRedBlocks) {
 
 // ---------------------------------------------------------------- kernels --
 // Stencils (k_stencil.cu).
+// Az (mode 1 only, MFG_CG_REF_RHS): AAt z_l on entry, b = AAt z_l + r on exit.
 void launch_apply_C(const Geom& g, const double* v, double* r, double alpha, const double* m0,
                     double* partials, DevScalars* sc, int mode, cudaStream_t s,
-                    const double* pdot = nullptr);
+                    const double* pdot = nullptr, double* Az = nullptr);
 void launch_apply_Ct(const Geom& g, const double* p, double* x, cudaStream_t s);
 // df64 != 0 selects the double-float variant of the stencil (MFG_MIXED_DF).
-// q = AAt p.  scratch: 2 n doubles.  mode 0: plain apply; 1: PCG step (p.q,
-// alpha); 2: ||AAt p + r2||^2 as the MFG_CG_REF_RHS stop reference (q unused).
+// q = AAt p.  scratch: 2 n doubles.  mode 0: plain apply; 1: PCG step (p.q, alpha).
 void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, double* partials,
-                DevScalars* sc, int mode, cudaStream_t s, int df64, const double* r2 = nullptr);
+                DevScalars* sc, int mode, cudaStream_t s, int df64);
 int aat_kernel_count(int df64);
 int aat_blocks(const Geom& g);
 
@@ -185,9 +185,12 @@ void launch_adj_grads(const Geom& g, const double* y, const double* z, const dou
                       double* partials, DevScalars* sc, cudaStream_t s);
 
 // Prox (k_prox.cu).
+// Az, rfin (MFG_CG_REF_RHS, else null): Az -= rfin turns the right-hand side b
+// into AAt z_{l+1} = b - r_final for the next iteration's stop reference.
 void launch_prox_cp(const Geom& g, const Coef& cf, const double* z, double* y, double* ybar,
                     const double* V, const double* W, double* partials, DevScalars* sc,
-                    cudaGraphConditionalHandle h, int use_handle, cudaStream_t s);
+                    cudaGraphConditionalHandle h, int use_handle, cudaStream_t s,
+                    double* Az = nullptr, const double* rfin = nullptr);
 void launch_prox_plain(const Geom& g, const Coef& cf, double tau, const double* v, double* y,
                        const double* V, const double* W, cudaStream_t s);
 
