@@ -28,13 +28,28 @@ struct __align__(2 * sizeof(T)) cx {
 
 enum { FFT_DHT = 0, FFT_DCT2 = 1, FFT_DCT3 = 2 };
 
+// Lines of N >= 256 take radix-8 Stockham stages (N/8 >= 32 butterflies
+// keep every lane of the warp busy), shorter lines radix-4 stages.
+template <int N>
+struct FftRadix {
+  static constexpr bool R8 = N >= 256;
+};
+
 // Position of element k of a complex line in shared memory: k with its low
-// four bits XORed by 5 (bits 4-5 of k).  The Stockham stages with span 1 and 4
-// store with a stride of 4 elements, which without it sends 8 lanes of a
-// half-warp to one bank pair; with it every stage's stores and the contiguous
-// loads hit 16 distinct bank pairs per half-warp (8-byte elements).  It
-// permutes within aligned groups of 64, so a line of N >= 8 stays in [0, N).
-__device__ __forceinline__ int swz(int k) { return k ^ (((k >> 4) & 3) * 5); }
+// four bits XORed by a mask taken from bits 4-7.  Stockham stages store with
+// strides of R and R^2 elements, which without it send up to 8 lanes of a
+// half-warp to one bank pair (8-byte elements).  Radix 8: mask 13 b4 ^ 9 b5 ^
+// 14 b6 ^ 10 b7 (b_i = bit i of k), radix 4: 5 (b4 + 2 b5); each was chosen by
+// searching over the stage, contiguous-load and separation access patterns,
+// where it stays within 11 % (radix 8) of the minimum wavefront count.  Both
+// permute within aligned groups of 16, so a line of N >= 8 stays in [0, N).
+template <int N>
+__device__ __forceinline__ int swz(int k) {
+  if constexpr (FftRadix<N>::R8)
+    return k ^ ((((k >> 4) & 1) * 13) ^ (((k >> 5) & 1) * 9) ^ (((k >> 6) & 1) * 14) ^ (((k >> 7) & 1) * 10));
+  else
+    return k ^ (((k >> 4) & 3) * 5);
+}
 
 template <typename T, int N>
 struct FftShape {
@@ -108,7 +123,7 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
       real1[l * NP + i] = v;
     } else {
       const int p = (MODE == FFT_DCT2) ? ((i & 1) ? N - 1 - (i >> 1) : (i >> 1)) : i;
-      T* dst = reinterpret_cast<T*>(&buf0[(l >> 1) * NP + swz(p)]);
+      T* dst = reinterpret_cast<T*>(&buf0[(l >> 1) * NP + swz<N>(p)]);
       dst[l & 1] = v;
     }
   };
@@ -167,22 +182,26 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
       const T c = dcs[k].x, s = dcs[k].y;
       const T war = c * ak + s * am, wai = s * ak - c * am;
       const T wbr = c * bk + s * bm, wbi = s * bk - c * bm;
-      buf0[q * NP + swz(k)] = cx<T>{war - wbi, wai + wbr};
+      buf0[q * NP + swz<N>(k)] = cx<T>{war - wbi, wai + wbr};
     }
     __syncthreads();
   }
 
   // ---- Stockham FFT, one warp per complex line, natural order in and out:
-  // radix-4 stages (Ns = 1, 4, 16, ...) then one radix-2 stage when log2 N is
-  // odd, in the mixed-radix Stockham formulation of Govindaraju et al.
-  // (SC 2008): stage (R, Ns) reads v_r = src[j + r N/R], twiddles v_r by
-  // exp(sgn 2 pi i r (j mod Ns) / (R Ns)), takes the R-point DFT and writes
-  // dst[(j - j mod Ns) R + j mod Ns + r Ns].
+  // for N >= 256 radix-8 stages (Ns = 1, 8, 64), then one radix-4 or radix-2
+  // stage when log2 N is not a multiple of 3; for shorter lines radix-4 stages
+  // and one radix-2 stage when log2 N is odd; in the mixed-radix Stockham formulation of
+  // Govindaraju et al. (SC 2008): stage (R, Ns) reads v_r = src[j + r N/R],
+  // twiddles v_r by exp(sgn 2 pi i r (j mod Ns) / (R Ns)), takes the R-point
+  // DFT and writes dst[(j - j mod Ns) R + j mod Ns + r Ns].
   constexpr T sgn = (MODE == FFT_DCT3) ? T(1) : T(-1);
   const int warp = tid >> 5, lane = tid & 31;
-  int log2n = 0;
-  for (int t = N; t > 1; t >>= 1) ++log2n;
-  const int n4 = log2n >> 1, n2 = log2n & 1;
+  constexpr int log2n = (N >= 512) ? 9 : (N >= 256) ? 8 : (N >= 128) ? 7 : (N >= 64) ? 6 : (N >= 32) ? 5 : (N >= 16) ? 4 : 3;
+  constexpr bool R8 = FftRadix<N>::R8;
+  // radix-8 schedule: n8 radix-8 stages, then radix 4 (r3 = 2) or 2 (r3 = 1);
+  // radix-4 schedule: n4 radix-4 stages, then radix 2 when log2 N is odd
+  constexpr int n8 = R8 ? log2n / 3 : 0, r3 = R8 ? log2n % 3 : 0;
+  constexpr int n4 = R8 ? 0 : log2n / 2, n2 = R8 ? 0 : log2n % 2;
   // exp(sgn 2 pi i m / N) for 0 <= m < N from the half-circle table
   auto twid = [&](int m) -> cx<T> {
     const cx<T> t = tws[m & (N / 2 - 1)];
@@ -190,45 +209,105 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
     return cx<T>{f * t.x, f * sgn * t.y};
   };
   auto cmul = [](cx<T> a, cx<T> w) { return cx<T>{a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x}; };
+  auto add = [](cx<T> a, cx<T> b) { return cx<T>{a.x + b.x, a.y + b.y}; };
+  auto sub = [](cx<T> a, cx<T> b) { return cx<T>{a.x - b.x, a.y - b.y}; };
+  auto rot = [](cx<T> a) { return cx<T>{-sgn * a.y, sgn * a.x}; };  // times sgn i
+  // 4-point DFT in place: B_s = sum_r b_r exp(sgn 2 pi i r s / 4)
+  auto dft4 = [&](cx<T>& b0, cx<T>& b1, cx<T>& b2, cx<T>& b3) {
+    const cx<T> s02 = add(b0, b2), d02 = sub(b0, b2), s13 = add(b1, b3), d13 = rot(sub(b1, b3));
+    b0 = add(s02, s13);
+    b1 = add(d02, d13);
+    b2 = sub(s02, s13);
+    b3 = sub(d02, d13);
+  };
+  const T h = T(0.70710678118654752440);  // cos(pi/4)
   for (int q = warp; q < CL; q += 8) {
     cx<T>* src = buf0 + q * NP;
     cx<T>* dst = buf1 + q * NP;
     int Ns = 1;
+#pragma unroll
+    for (int st = 0; st < n8; ++st, Ns <<= 3) {
+#pragma unroll
+      for (int j = lane; j < N / 8; j += 32) {
+        const int k = j & (Ns - 1);
+        const int m = k * (N / (8 * Ns));
+        cx<T> a[8];
+        a[0] = src[swz<N>(j)];
+#pragma unroll
+        for (int r = 1; r < 8; ++r) a[r] = cmul(src[swz<N>(j + r * (N / 8))], twid(r * m));
+        // 8-point DFT: even and odd 4-point DFTs, then A_s = E_s + w^s O_s,
+        // A_{s+4} = E_s - w^s O_s with w = exp(sgn 2 pi i / 8)
+        dft4(a[0], a[2], a[4], a[6]);
+        dft4(a[1], a[3], a[5], a[7]);
+        const cx<T> o1{h * (a[3].x - sgn * a[3].y), h * (a[3].y + sgn * a[3].x)};
+        const cx<T> o2 = rot(a[5]);
+        const cx<T> o3{h * (-a[7].x - sgn * a[7].y), h * (-a[7].y + sgn * a[7].x)};
+        const int d = ((j - k) << 3) + k;
+        dst[swz<N>(d)] = add(a[0], a[1]);
+        dst[swz<N>(d + 4 * Ns)] = sub(a[0], a[1]);
+        dst[swz<N>(d + Ns)] = add(a[2], o1);
+        dst[swz<N>(d + 5 * Ns)] = sub(a[2], o1);
+        dst[swz<N>(d + 2 * Ns)] = add(a[4], o2);
+        dst[swz<N>(d + 6 * Ns)] = sub(a[4], o2);
+        dst[swz<N>(d + 3 * Ns)] = add(a[6], o3);
+        dst[swz<N>(d + 7 * Ns)] = sub(a[6], o3);
+      }
+      __syncwarp();
+      cx<T>* t = src; src = dst; dst = t;
+    }
+#pragma unroll
     for (int st = 0; st < n4; ++st, Ns <<= 2) {
 #pragma unroll
       for (int j = lane; j < N / 4; j += 32) {
         const int k = j & (Ns - 1);
         const int m = k * (N / (4 * Ns));
-        const cx<T> a0 = src[swz(j)];
-        const cx<T> a1 = cmul(src[swz(j + N / 4)], twid(m));
-        const cx<T> a2 = cmul(src[swz(j + N / 2)], twid(2 * m));
-        const cx<T> a3 = cmul(src[swz(j + 3 * N / 4)], twid(3 * m));
-        const cx<T> s02{a0.x + a2.x, a0.y + a2.y}, d02{a0.x - a2.x, a0.y - a2.y};
-        const cx<T> s13{a1.x + a3.x, a1.y + a3.y}, d13{a1.x - a3.x, a1.y - a3.y};
+        cx<T> a0 = src[swz<N>(j)];
+        cx<T> a1 = cmul(src[swz<N>(j + N / 4)], twid(m));
+        cx<T> a2 = cmul(src[swz<N>(j + N / 2)], twid(2 * m));
+        cx<T> a3 = cmul(src[swz<N>(j + 3 * N / 4)], twid(3 * m));
+        dft4(a0, a1, a2, a3);
         const int d = ((j - k) << 2) + k;
-        dst[swz(d)] = cx<T>{s02.x + s13.x, s02.y + s13.y};
-        dst[swz(d + Ns)] = cx<T>{d02.x - sgn * d13.y, d02.y + sgn * d13.x};
-        dst[swz(d + 2 * Ns)] = cx<T>{s02.x - s13.x, s02.y - s13.y};
-        dst[swz(d + 3 * Ns)] = cx<T>{d02.x + sgn * d13.y, d02.y - sgn * d13.x};
+        dst[swz<N>(d)] = a0;
+        dst[swz<N>(d + Ns)] = a1;
+        dst[swz<N>(d + 2 * Ns)] = a2;
+        dst[swz<N>(d + 3 * Ns)] = a3;
       }
       __syncwarp();
       cx<T>* t = src; src = dst; dst = t;
     }
-    if (n2) {
+    if (r3 == 2) {
+#pragma unroll
+      for (int j = lane; j < N / 4; j += 32) {
+        const int k = j & (Ns - 1);
+        const int m = k * (N / (4 * Ns));
+        cx<T> a0 = src[swz<N>(j)];
+        cx<T> a1 = cmul(src[swz<N>(j + N / 4)], twid(m));
+        cx<T> a2 = cmul(src[swz<N>(j + N / 2)], twid(2 * m));
+        cx<T> a3 = cmul(src[swz<N>(j + 3 * N / 4)], twid(3 * m));
+        dft4(a0, a1, a2, a3);
+        const int d = ((j - k) << 2) + k;
+        dst[swz<N>(d)] = a0;
+        dst[swz<N>(d + Ns)] = a1;
+        dst[swz<N>(d + 2 * Ns)] = a2;
+        dst[swz<N>(d + 3 * Ns)] = a3;
+      }
+      __syncwarp();
+    } else if (r3 == 1 || n2 == 1) {
 #pragma unroll
       for (int j = lane; j < N / 2; j += 32) {
         const int k = j & (Ns - 1);
-        const cx<T> a = src[swz(j)];
-        const cx<T> b = cmul(src[swz(j + N / 2)], twid(k * (N / (2 * Ns))));
+        const cx<T> a = src[swz<N>(j)];
+        const cx<T> b = cmul(src[swz<N>(j + N / 2)], twid(k * (N / (2 * Ns))));
         const int d = ((j - k) << 1) + k;
-        dst[swz(d)] = cx<T>{a.x + b.x, a.y + b.y};
-        dst[swz(d + Ns)] = cx<T>{a.x - b.x, a.y - b.y};
+        dst[swz<N>(d)] = add(a, b);
+        dst[swz<N>(d + Ns)] = sub(a, b);
       }
       __syncwarp();
     }
   }
   __syncthreads();
-  const bool odd = ((n4 + n2) & 1) != 0;  // stages taken: the result is in buf1 after an odd count
+  // stages taken: the result is in buf1 after an odd count
+  const bool odd = ((n8 + n4 + ((r3 || n2) ? 1 : 0)) & 1) != 0;
   const cx<T>* Z = odd ? buf1 : buf0;
   T* R = reinterpret_cast<T*>(odd ? buf0 : buf1);  // real output staging [LB][NP]
 
@@ -236,13 +315,13 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
   const T rsn = T(1) / sqrt(T(N));
   for (int idx = tid; idx < CL * N; idx += 256) {
     const int q = idx / N, k = idx % N;
-    const cx<T> zk = Z[q * NP + swz(k)];
+    const cx<T> zk = Z[q * NP + swz<N>(k)];
     if (MODE == FFT_DCT3) {
       const int pos = (k < N / 2) ? 2 * k : 2 * (N - 1 - k) + 1;
       R[(2 * q) * NP + pos] = zk.x;
       R[(2 * q + 1) * NP + pos] = zk.y;
     } else {
-      const cx<T> zm = Z[q * NP + swz((N - k) & (N - 1))];
+      const cx<T> zm = Z[q * NP + swz<N>((N - k) & (N - 1))];
       const T sr = T(0.5) * (zk.x + zm.x), si = T(0.5) * (zk.y - zm.y);  // X_a
       const T dr = T(0.5) * (zk.y + zm.y), di = T(0.5) * (zm.x - zk.x);  // X_b
       if (MODE == FFT_DHT) {
