@@ -249,6 +249,40 @@ def problem2(N=16, nt=None, nu=0.01, beta=1e-3):
     return _inst(prob, m0, V, W, initial_iterate(prob, m0), m_target=mbar)
 
 
+def viscosity_field(prob, nu0, ratio, seed, kind="smooth"):
+    """Seeded viscosity field nu(x) (shape (Nx, Ny)) with max/min = ratio and
+    geometric centre nu0.  kind "smooth": nu0 * ratio**(u/2) with u a random
+    cosine series (4 modes per axis, PCG64(seed)) rescaled to [-1, 1];
+    kind "layers": nu0 / sqrt(ratio) on one side of a seeded straight interface
+    and nu0 * sqrt(ratio) on the other (a discontinuous coefficient)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X, Y = nodes(prob)
+    lx, ly = prob["len"]
+    if kind == "layers":
+        ang = rng.uniform(0.0, np.pi)
+        c = rng.uniform(0.35, 0.65)
+        side = np.cos(ang) * (X / lx - c) + np.sin(ang) * (Y / ly - c) > 0
+        return np.where(side, nu0 * np.sqrt(ratio), nu0 / np.sqrt(ratio))
+    u = np.zeros_like(X)
+    for _ in range(4):
+        kx, ky = rng.integers(0, 4, size=2)
+        ph = rng.uniform(0.0, 2.0 * np.pi, size=2)
+        u += rng.normal() * np.cos(np.pi * kx * X / lx + ph[0]) * np.cos(np.pi * ky * Y / ly + ph[1])
+    span = u.max() - u.min()
+    u = 2.0 * (u - u.min()) / span - 1.0 if span > 0 else np.zeros_like(u)
+    return nu0 * ratio ** (0.5 * u)
+
+
+def config_varnu(n=128, nt=64, nu=1e-2, ratio=10.0, kind="smooth"):
+    """2-D Neumann unit square with a viscosity field nu(x) (seed 7, max/min =
+    ratio around nu), otherwise the Neumann workload's fields: V a seeded cosine
+    series (seed 3), g = 0.1 |x - (0.8,0.8)|^2, m0 a Gaussian at (0.2, 0.2),
+    sigma 0.08."""
+    inst = config3(n=n, nt=nt, nu=nu)
+    inst["problem"]["nu_field"] = viscosity_field(inst["problem"], nu, ratio, 7, kind)
+    return inst
+
+
 def small(seed, dim=2, nx=None, ny=None, nt=None, bc=None, nu=None, l=None,
           f_a=None, g_a=None, eps=1e-2, max_cp=20):
     """Small random instance for parity tests: ragged sizes, random fields."""

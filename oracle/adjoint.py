@@ -123,7 +123,10 @@ def loss_mT(prob, y, m_target):
 
 def adjoint_gradients(prob, y, z, gy):
     """Solve K [mu; eta] = [g_A; 0] and contract: returns dict of dm0 (Nx, Ny),
-    dV (Nx, Ny), dW (Nx, Ny), dnu (float), plus mu, eta."""
+    dV (Nx, Ny), dW (Nx, Ny), dnu (float), plus mu, eta.  Constant viscosity
+    only (dnu is the derivative in the scalar nu)."""
+    if ops.has_nu_field(prob):
+        raise ValueError("adjoint_gradients: constant viscosity only")
     C = ops.constraint(prob)
     act = active_mask(y)
     a = act.reshape(-1)

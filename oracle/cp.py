@@ -19,6 +19,8 @@ with method="pcg", inexact as in Sec. 5: preconditioned CG with the paper's P
 fixed prob["cg_tol"] or at the adaptive min{1e-4, max{1e-6, 1e-4 r}} of Sec. 5
 (prob["cg_rule"] = 1), relative either to the residual of the warm start
 (cg_ref="resid") or to the right-hand side of the full system (cg_ref="rhs").
+With a viscosity field nu(x) (prob["nu_field"]) the exact solve is sparse LU
+and the PCG preconditioner is Alg. 1 with a sparse LU per time frequency.
 Start: tau_0 = sigma_0 = 1, x_0 = 0, ybar_0 = y_0.
 """
 from __future__ import annotations
@@ -58,7 +60,7 @@ class Solver:
         self.d = ops.rhs_d(prob, m0)
         self.V, self.W = V, W
         if method == "auto":
-            method = "lu" if n <= 40000 else "modal"
+            method = "lu" if (n <= 40000 or ops.has_nu_field(prob)) else "modal"
         self.method = method
         self.cg_ref = cg_ref
         if method == "lu":
@@ -73,7 +75,10 @@ class Solver:
         """Inexact solve of C C^T z = b by PCG from z0 (Sec. 5); returns (z, iterations)."""
         p = self.prob
         apply_A = lambda v: self.C @ (self.CT @ v)
-        if p["l"] == 0:
+        if ops.has_nu_field(p):
+            # a viscosity field: Alg. 1 with one sparse LU per time frequency
+            apply_Minv = lambda r: solvers.precond_lu(p, r)
+        elif p["l"] == 0:
             apply_Minv = lambda r: solvers.solve_AAt_modal(p, r)
         else:
             apply_Minv = lambda r: solvers.precond_modal(p, r)

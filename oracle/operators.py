@@ -78,11 +78,67 @@ def spatial(prob):
     return B, K
 
 
-def L_matrix(prob, K=None):
-    """L = nu K + I/dt (Sec. 3, below the matrices A and B)."""
+def has_nu_field(prob):
+    """True when the problem carries a viscosity field nu(x) (prob["nu_field"],
+    one value per node, shape (Nx, Ny)) instead of the constant prob["nu"]."""
+    return prob.get("nu_field") is not None
+
+
+def nu_faces(prob):
+    """Face viscosities of a field nu(x): on each active axis, face i sits
+    between node i and node i+1 (wrapping on a periodic axis) and takes the
+    arithmetic mean of the two node values; the face past the end of a Neumann
+    axis joins no second node and carries 0.  Returns one (Nx, Ny) array per
+    active axis (x, then y in 2-D)."""
+    nx, ny = prob["n"]
+    nu = np.asarray(prob["nu_field"], dtype=np.float64).reshape(nx, ny)
+    out = []
+    for ax in range(prob["dim"]):
+        nb = np.roll(nu, -1, axis=ax)
+        f = 0.5 * (nu + nb)
+        if prob["bc"][ax] != PERIODIC:
+            idx = [slice(None), slice(None)]
+            idx[ax] = -1
+            f[tuple(idx)] = 0.0
+        out.append(f)
+    return out
+
+
+def K_nu(prob):
+    """Variable-coefficient negative Laplacian -div(nu grad) in the paper's
+    difference form: per axis D^1 diag(nu_face) (D^1)^T / dx^2 with the D^1
+    blocks of Sec. 4.3 (columns = faces, face i between nodes i and i+1), summed
+    over the axes as K is.  A constant field gives nu K exactly.  The paper
+    allows nu(x) without fixing its discretisation (Sec. 4, before Sec. 4.1);
+    this is the symmetric conservative reading, which keeps L symmetric so
+    that C = L^2 + B B^T and the block forms of Sec. 4.1 hold unchanged."""
+    nx, ny = prob["n"]
+    dx, dy = spacing(prob)
+    faces = nu_faces(prob)
+    d1x, _ = div_blocks(nx, prob["bc"][0])
+    if prob["dim"] == 1:
+        return (d1x @ sp.diags(faces[0].reshape(-1)) @ d1x.T / dx ** 2).tocsr()
+    d1y, _ = div_blocks(ny, prob["bc"][1])
+    Dx = sp.kron(d1x, sp.identity(ny))
+    Dy = sp.kron(sp.identity(nx), d1y)
+    return (Dx @ sp.diags(faces[0].reshape(-1)) @ Dx.T / dx ** 2 +
+            Dy @ sp.diags(faces[1].reshape(-1)) @ Dy.T / dy ** 2).tocsr()
+
+
+def viscous(prob, K=None):
+    """The viscous term of L: nu K for a constant nu, K_nu for a field."""
+    if has_nu_field(prob):
+        return K_nu(prob)
     if K is None:
         _, K = spatial(prob)
-    return (prob["nu"] * K + sp.identity(K.shape[0]) / dt(prob)).tocsr()
+    return (prob["nu"] * K).tocsr()
+
+
+def L_matrix(prob, K=None):
+    """L = nu K + I/dt (Sec. 3, below the matrices A and B); K_nu + I/dt for a
+    viscosity field."""
+    Kv = viscous(prob, K)
+    return (Kv + sp.identity(Kv.shape[0]) / dt(prob)).tocsr()
 
 
 def constraint(prob):
@@ -113,7 +169,8 @@ def apply_C_planes(prob, v):
     m = v[0]
     w = np.concatenate([v[q] for q in range(1, c)], axis=1)  # (nt, (c-1) s) in the w order of B
     h = dt(prob)
-    out = prob["nu"] * (K @ m.T).T + m / h + (B @ w.T).T
+    Kv = viscous(prob, K)
+    out = (Kv @ m.T).T + m / h + (B @ w.T).T
     out[1:] -= m[:-1] / h
     return out.reshape(-1)
 
@@ -128,7 +185,7 @@ def apply_Ct_planes(prob, p):
     c = n_planes(prob)
     p = np.asarray(p, dtype=np.float64).reshape(nt, s)
     h = dt(prob)
-    xm = prob["nu"] * (K @ p.T).T + p / h
+    xm = (viscous(prob, K) @ p.T).T + p / h
     xm[:-1] -= p[1:] / h
     xw = (B.T @ p.T).T  # (nt, (c-1) s)
     out = np.empty((c, nt, s))
@@ -162,10 +219,12 @@ def Dtt(nt, l):
 
 def precond(prob):
     """P = I_Nt (x) C_hat + D_tt (x) L_hat with C_hat = nu^2 K^2 + B B^T and
-    L_hat = L/dt (Sec. 4.1 eq. prec and its Kronecker form)."""
+    L_hat = L/dt (Sec. 4.1 eq. prec and its Kronecker form); for a viscosity
+    field nu K becomes K_nu, so C_hat = K_nu^2 + B B^T."""
     B, K = spatial(prob)
     L = L_matrix(prob, K)
-    C_hat = prob["nu"] ** 2 * (K @ K) + B @ B.T
+    Kv = viscous(prob, K)
+    C_hat = Kv @ Kv + B @ B.T
     L_hat = L / dt(prob)
     nt = prob["nt"]
     return (sp.kron(sp.identity(nt), C_hat) + sp.kron(Dtt(nt, prob["l"]), L_hat)).tocsr()

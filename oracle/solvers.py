@@ -17,9 +17,10 @@ import os
 import numpy as np
 import scipy.fft as sfft
 import scipy.linalg as sla
+import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .operators import PERIODIC, dt, spacing
+from .operators import PERIODIC, Dtt, dt, has_nu_field, nu_faces, spacing, spatial, viscous
 
 
 # threads of the FFT library (all host cores; the transforms are the same)
@@ -123,10 +124,16 @@ def _shape(prob):
     return prob["nt"], nx, ny
 
 
+def _constant_nu(prob, what):
+    if has_nu_field(prob):
+        raise ValueError(what + " needs a constant viscosity (the spatial eigenbasis of K)")
+
+
 def solve_AAt_modal(prob, b):
     """Exact solve of AAt z = b.  Per spatial mode s with eigenvalue kappa:
     L_s = nu kappa + 1/dt, C_s = L_s^2 + 2 kappa; diagonal (C_s, C_s + 1/dt^2, ...),
     off-diagonal -L_s/dt (eq. largeA with B B^T = 2K)."""
+    _constant_nu(prob, "solve_AAt_modal")
     nt, nx, ny = _shape(prob)
     kap = laplacian_eigs(prob)
     h = dt(prob)
@@ -143,6 +150,7 @@ def precond_modal(prob, r):
     """Exact P^{-1} r for eq. prec: per spatial mode, C_hat_s = nu^2 kappa^2 + 2 kappa,
     L_hat_s = (nu kappa + 1/dt)/dt, diagonal (C_hat + l L_hat, C_hat + 2 L_hat, ...),
     off-diagonal -L_hat (no time transform involved)."""
+    _constant_nu(prob, "precond_modal")
     nt, nx, ny = _shape(prob)
     kap = laplacian_eigs(prob)
     h = dt(prob)
@@ -161,6 +169,7 @@ def eig_range_AAt(prob):
     spatial mode (the blocks of solve_AAt_modal), so its spectrum is the union
     of theirs; each block's extreme eigenvalues come from LAPACK's tridiagonal
     eigensolver.  Modes with equal Laplacian eigenvalue share a block."""
+    _constant_nu(prob, "eig_range_AAt")
     nt, kap, h = _modal_blocks(prob)
     lo, hi = np.inf, -np.inf
     for k in np.unique(kap):
@@ -198,6 +207,7 @@ def apply_AAt_modal(prob, p):
     """AAt p through the spatial eigenbasis (same blocks as solve_AAt_modal,
     multiplied instead of solved): a matrix-free AAt for grids too large to
     assemble."""
+    _constant_nu(prob, "apply_AAt_modal")
     nt, kap, h = _modal_blocks(prob)
     nx, ny = prob["n"]
     Ls = prob["nu"] * kap + 1.0 / h
@@ -211,6 +221,7 @@ def apply_AAt_modal(prob, p):
 def apply_P_modal(prob, z):
     """P z for the preconditioner of eq. prec, through the spatial eigenbasis;
     also returns the largest eigenvalue of P (its 2-norm)."""
+    _constant_nu(prob, "apply_P_modal")
     nt, kap, h = _modal_blocks(prob)
     nx, ny = prob["n"]
     Lh = (prob["nu"] * kap + 1.0 / h) / h
@@ -243,3 +254,113 @@ def pcg(apply_A, apply_Minv, b, tol, x0=None, maxiter=10000):
         rz = rz_new
         it += 1
     return x, it
+
+
+# ------------------------------------------------------------ nu(x) field --
+# With a viscosity field the spatial blocks are no longer polynomials in K, so
+# the per-frequency systems of Alg. 1 are solved as sparse matrices.
+
+
+def time_basis(nt, l):
+    """Orthonormal eigenvectors Q (columns) and eigenvalues of D_tt with first
+    entry l (Sec. 4.1: the DCT-VIII basis for l = 1, DST-I for l = 2), from
+    LAPACK's symmetric eigensolver on the assembled N_t x N_t matrix."""
+    lam, Q = np.linalg.eigh(Dtt(nt, l).toarray())
+    return Q, lam
+
+
+def _prec_blocks(prob):
+    """C_hat = K_nu^2 + B B^T and L_hat = (K_nu + I/dt)/dt of eq. prec."""
+    B, K = spatial(prob)
+    Kv = viscous(prob, K)
+    h = dt(prob)
+    ident = sp.identity(Kv.shape[0])
+    return (Kv @ Kv + B @ B.T).tocsc(), ((Kv + ident / h) / h).tocsc()
+
+
+def precond_lu(prob, r):
+    """P^{-1} r by Alg. 1: time transform (P = (Q (x) I) diag_k(C_hat +
+    lambda_k L_hat) (Q^T (x) I) with D_tt = Q Lambda Q^T), one sparse LU solve
+    per time frequency (the paper's first option for the per-step systems,
+    Sec. 4.1 after Alg. 1), inverse time transform.  Any viscosity, l in {1, 2}."""
+    if prob["l"] not in (1, 2):
+        raise ValueError("precond_lu: l must be 1 or 2")
+    nt = prob["nt"]
+    Q, lam = time_basis(nt, prob["l"])
+    Ch, Lh = _prec_blocks(prob)
+    R = np.asarray(r, dtype=np.float64).reshape(nt, -1)
+    Yh = Q.T @ R
+    Xh = np.empty_like(Yh)
+    for k in range(nt):
+        Xh[k] = spla.splu((Ch + lam[k] * Lh).tocsc()).solve(Yh[k])
+    return (Q @ Xh).reshape(-1)
+
+
+def nu_ref(prob):
+    """Reference viscosity of the constant-coefficient spatial solve that
+    preconditions the per-frequency systems for a field nu(x): the geometric
+    mean sqrt(min * max) of the live face viscosities (faces past a Neumann
+    end excluded), the value that balances the extreme ratios nu_face/nu_ref."""
+    vals = []
+    for ax, f in enumerate(nu_faces(prob)):
+        if prob["bc"][ax] != PERIODIC:
+            idx = [slice(None), slice(None)]
+            idx[ax] = slice(0, -1)
+            f = f[tuple(idx)]
+        vals.append(f.reshape(-1))
+    v = np.concatenate(vals)
+    return float(np.sqrt(v.min() * v.max()))
+
+
+def _mbar_inv(prob, nub, lam_k, v):
+    """(C_hat + lambda_k L_hat)^{-1} v for the constant viscosity nub: diagonal
+    in the spatial eigenbasis of K (Alg. 2), eigenvalue
+    nub^2 kappa^2 + 2 kappa + lambda_k (nub kappa + 1/dt)/dt."""
+    nx, ny = prob["n"]
+    kap = laplacian_eigs(prob)
+    h = dt(prob)
+    den = nub ** 2 * kap ** 2 + 2.0 * kap + lam_k * (nub * kap + 1.0 / h) / h
+    vh = to_modes(prob, np.asarray(v, dtype=np.float64).reshape(1, nx, ny))
+    return np.real(from_modes(prob, vh / den[None])).reshape(-1)
+
+
+def precond_inner(prob, r, s):
+    """Alg. 1 with inexact per-frequency solves: for each time frequency k,
+    `s` steps of preconditioned CG on (C_hat + lambda_k L_hat) x = y_k from
+    x = 0, preconditioned by the same block with the constant viscosity
+    nu_ref(prob) (solved exactly in the spatial eigenbasis); s = 0 applies that
+    constant-coefficient block alone.  A step whose curvature p.Mp is not
+    positive, or whose r.z vanishes, contributes nothing (alpha = beta = 0).
+    Exact for a constant field with s >= 1; tends to precond_lu as s grows."""
+    nt = prob["nt"]
+    Q, lam = time_basis(nt, prob["l"])
+    Ch, Lh = _prec_blocks(prob)
+    nub = nu_ref(prob)
+    R = np.asarray(r, dtype=np.float64).reshape(nt, -1)
+    Yh = Q.T @ R
+    Xh = np.zeros_like(Yh)
+    for k in range(nt):
+        M = (Ch + lam[k] * Lh).tocsr()
+        res = Yh[k].copy()
+        z = _mbar_inv(prob, nub, lam[k], res)
+        if s == 0:
+            Xh[k] = z
+            continue
+        p = z.copy()
+        rz = res @ z
+        x = np.zeros_like(res)
+        for i in range(s):
+            q = M @ p
+            pq = p @ q
+            alpha = rz / pq if (pq > 0 and np.isfinite(pq)) else 0.0
+            x += alpha * p
+            if i == s - 1:
+                break
+            res -= alpha * q
+            z = _mbar_inv(prob, nub, lam[k], res)
+            rz_new = res @ z
+            beta = rz_new / rz if rz > 0 else 0.0
+            rz = rz_new
+            p = z + beta * p
+        Xh[k] = x
+    return (Q @ Xh).reshape(-1)
