@@ -103,7 +103,37 @@ typedef struct {
   int max_cg;        /* PCG iteration cap per solve                                    */
   int precision;     /* MFG_FP64 | MFG_MIXED | MFG_MIXED_DF | MFG_MIXED_TC             */
   int cg_ref;        /* MFG_CG_REF_RHS (0, the default) | MFG_CG_REF_RESID             */
+  const double* nu_field; /* NULL: constant viscosity nu.  Otherwise a HOST array of
+                        Nx*Ny node viscosities nu(x) >= 0 ([Nx][Ny], read during
+                        mfg_plan only, never retained), which replaces nu; see
+                        "Viscosity fields" below.                                    */
 } mfg_problem;
+
+/* Viscosity fields (nu_field != NULL).  The paper allows a non-constant
+ * viscosity nu(x) (Sec. 4, before Sec. 4.1: the spatial matrices still repeat
+ * at every time step) without fixing its discretisation.  Here nu K becomes
+ *   K_nu = sum over the active axes of D^1 diag(nu_face) (D^1)^T / dx^2,
+ * with the D^1 blocks of Sec. 4.3, face i of an axis between nodes i and i+1
+ * (wrapping on a periodic axis) and nu_face the arithmetic mean of those two
+ * node values: a symmetric conservative operator, so L = K_nu + I/dt is
+ * symmetric, C = L^2 + B B^T, and eq. largeA and eq. prec keep their block
+ * forms with C_hat = K_nu^2 + B B^T and L_hat = L/dt.  The constraint, its
+ * transpose, AAt and the dual lift of the prox step use K_nu.
+ * The preconditioner is Alg. 1 with an exact solve of every per-frequency
+ * system (C_hat + lambda_k L_hat) x_k = y_k, the LU option of Sec. 4.1: a
+ * banded Cholesky factorisation per time frequency, formed once in FP64 by
+ * mfg_plan on the host (points ordered axis by axis, a periodic axis folded
+ * 0, N-1, 1, N-2, ... so that the bandwidth stays ~2-4 Ny), stored on the
+ * device in the plan's preconditioner precision (FP32 for the MIXED
+ * precisions), and applied per frequency by forward and backward banded
+ * substitution between the two time transforms.  Costs: factor storage
+ * 2 N_t Nx Ny (w+1) words, w the half-bandwidth (2 Ny on a Neumann x axis,
+ * ~4 Ny + Ny on a periodic one), and O(N_t Nx Ny w^2) host work in mfg_plan.
+ * Restrictions: l must be 1 or 2 (MFG_ERR_UNSUPPORTED for l = 0); w <= 4096
+ * and factor storage <= 64 GiB (MFG_ERR_UNSUPPORTED beyond); mfg_adjoint and
+ * mfg_apply_precond_noalloc return MFG_ERR_UNSUPPORTED; MFG_MIXED_DF runs its
+ * AAt stencil in FP64 (as MFG_MIXED); the time transforms run on the CUDA cores
+ * in every precision.  nu is ignored. */
 
 /* Per-instance run record.  On entry to mfg_solve, `ell`, `tau`, `sigma` are
  * the resume state (ell = 0 starts from tau0, sigma0); on return all fields
@@ -124,8 +154,9 @@ typedef struct mfg_plan_s* mfg_plan_t;
  * and transform matrices on the host in FP64, uploads them and
  * allocates all device workspace on the current device.  Rejects q' outside
  * [1.05, 20] (MFG_ERR_UNSUPPORTED), N_t < 2, N < 2, T <= 0, nu < 0,
- * f_a/f_b/g_a < 0, l not in {0,1,2}, N_t > 256 (UNSUPPORTED).  *out is NULL on
- * failure. */
+ * f_a/f_b/g_a < 0, l not in {0,1,2}, N_t > 256 (UNSUPPORTED), a viscosity
+ * field with a negative or non-finite value (INVALID_ARG) or outside the
+ * limits of "Viscosity fields" (UNSUPPORTED).  *out is NULL on failure. */
 int mfg_plan(const mfg_problem* probs, int batch, mfg_plan_t* out);
 
 /* Frees all plan-owned memory.  NULL is accepted. */
@@ -169,8 +200,9 @@ int mfg_solve_host(mfg_plan_t plan, const double* m0, const double* V,
 /* z = P^{-1} r for instance b (Alg. 1 with Alg. 2 for its per-frequency
  * spatial solves, eq. pstrec), in the plan's precision.  With l = 0 the time transform and the
  * per-frequency division are replaced by an exact tridiagonal solve in time per
- * spatial mode, so P = AAt (eq. largeA) up to rounding.  r, z: n elements;
- * must not alias. */
+ * spatial mode, so P = AAt (eq. largeA) up to rounding.  With a viscosity
+ * field the per-frequency systems are solved by their banded Cholesky factors
+ * (see "Viscosity fields").  r, z: n elements; must not alias. */
 int mfg_apply_precond(mfg_plan_t plan, int b, const double* r, double* z, void* stream);
 
 /* y = prox_{tau phi}(v) for instance b, cell by cell (Sec. 3; phi_ij = b_hat +
@@ -212,7 +244,7 @@ int mfg_apply_Ct(mfg_plan_t plan, int b, const double* p, double* x, void* strea
  *   dW     : out, dloss/dW(x), Nx*Ny or NULL dnu: out, dloss/dnu, 1 device double
  *   tol, max_iter: relative tolerance and cap of the adjoint PCG
  *   st     : out; cg_iters = adjoint PCG iterations, r_last = final relative residual
- * Built for q' = 2 (MFG_ERR_UNSUPPORTED otherwise).
+ * Built for q' = 2 and a constant viscosity (MFG_ERR_UNSUPPORTED otherwise).
  * The adjoint system is solved through its Schur complement
  * C_A H^{-1} C_A^T with the plan's preconditioner P (eq. prec) inside PCG,
  * H being the per-cell Hessian of phi.  The first call allocates a c*n + n
@@ -310,8 +342,8 @@ int mfg_set_fault_injection(mfg_plan_t plan, int what);
  *     p->precision: MFG_FP64 and MFG_MIXED as in a plan, MFG_MIXED_TC with the
  *     tensor-core time pass as in a plan; MFG_MIXED_DF runs as MFG_MIXED (the
  *     two differ only in the AAt stencil, which this apply does not use).
- *     l = 0 (the exact time solve) needs plan-built factors and returns
- *     MFG_ERR_UNSUPPORTED. */
+ *     l = 0 (the exact time solve) and viscosity fields need plan-built
+ *     factors and return MFG_ERR_UNSUPPORTED. */
 int mfg_apply_precond_noalloc(const mfg_problem* p, const double* r, double* z, void* stream);
 
 #ifdef __cplusplus

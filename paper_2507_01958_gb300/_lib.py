@@ -30,7 +30,7 @@ class MfgProblem(C.Structure):
                 ("gamma", C.c_double), ("tau0", C.c_double), ("sigma0", C.c_double),
                 ("max_cp", C.c_int), ("cp_tol", C.c_double), ("cg_rule", C.c_int),
                 ("cg_tol", C.c_double), ("max_cg", C.c_int), ("precision", C.c_int),
-                ("cg_ref", C.c_int)]
+                ("cg_ref", C.c_int), ("nu_field", C.POINTER(C.c_double))]
 
 
 class MfgStats(C.Structure):
@@ -121,7 +121,8 @@ def problem_struct(d, precision=None):
     (FP32 preconditioner, MFG_MIXED), "mixed_tc" (its time transforms on the
     tensor cores, MFG_MIXED_TC), "mixed_df" (double-float AAt, MFG_MIXED_DF),
     or the integer code.  d["cg_ref"] (default "rhs"): "rhs" (MFG_CG_REF_RHS)
-    or "resid" (MFG_CG_REF_RESID), or the integer code."""
+    or "resid" (MFG_CG_REF_RESID), or the integer code.  d["nu_field"] (optional,
+    (Nx, Ny) array): the viscosity field nu(x) in place of nu."""
     p = MfgProblem()
     p.dim = d["dim"]
     p.n[0], p.n[1] = d["n"]
@@ -137,6 +138,14 @@ def problem_struct(d, precision=None):
                    "mixed_tc": MFG_MIXED_TC}.get(prec, prec)
     ref = d.get("cg_ref", "rhs")
     p.cg_ref = {"rhs": MFG_CG_REF_RHS, "resid": MFG_CG_REF_RESID}.get(ref, ref)
+    field = d.get("nu_field")
+    if field is not None:
+        # host copy of the node viscosities, kept alive with the struct (the
+        # library reads it only inside the call that takes the struct)
+        import numpy as np
+        buf = np.ascontiguousarray(np.asarray(field, dtype=np.float64).reshape(-1))
+        p._nu_buf = buf
+        p.nu_field = buf.ctypes.data_as(C.POINTER(C.c_double))
     return p
 
 
@@ -163,9 +172,10 @@ class Plan:
 def mfg_plan(problems, precision=None):
     if isinstance(problems, dict):
         problems = [problems]
-    arr = (MfgProblem * len(problems))(*[problem_struct(d, precision) for d in problems])
+    structs = [problem_struct(d, precision) for d in problems]  # keeps any field buffers alive
+    arr = (MfgProblem * len(structs))(*structs)
     h = C.c_void_p()
-    _check(LIB.mfg_plan(arr, len(problems), C.byref(h)))
+    _check(LIB.mfg_plan(arr, len(structs), C.byref(h)))
     return Plan(h.value, len(problems), [d["nt"] for d in problems])
 
 

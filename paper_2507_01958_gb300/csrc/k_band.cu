@@ -1,0 +1,468 @@
+// Viscosity fields nu(x): Alg. 1 of Sec. 4 with an exact solve of every
+// per-frequency system, the LU option the paper names for the per-time-step
+// systems (Sec. 4.1, after Alg. 1).
+//
+// With K_nu = sum_axes D^1 diag(nu_face) (D^1)^T / dx^2 in place of nu K, the
+// blocks of eq. prec are C_hat = K_nu^2 + B B^T = K_nu^2 + 2K (eq. precstead)
+// and L_hat = (K_nu + I/dt)/dt.  The time transform V (DCT-VIII or DST-I,
+// symmetric and orthonormal) still block-diagonalises P:
+//   P^{-1} r = V diag_k (C_hat + lambda_k L_hat)^{-1} V r,
+// but the spatial blocks no longer share the Laplacian's eigenbasis.  Each
+// M_k = C_hat + lambda_k L_hat is SPD and banded once the points are ordered
+// axis by axis (a periodic axis folded 0, N-1, 1, N-2, ... so that wrapped
+// neighbours stay close), so it is factored M_k = L_k L_k^T by banded
+// Cholesky on the host in FP64, once per plan.  An apply is
+//   time forward (scatter to band order) -> L y = b -> L^T x = y -> time
+//   inverse (gather from band order).
+// The substitutions are sequential along the band: one CTA per frequency
+// walks its S points with a circular window of w+2 partial sums in shared
+// memory; the factor rows, contiguous in memory in the order they are used,
+// stream through a ring of shared-memory stages filled by cp.async several
+// stages ahead, so the loads never wait on the dependency chain.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "mfg_internal.cuh"
+
+namespace mfg {
+
+namespace {
+
+constexpr int kBandRing = 4;           // shared-memory stages of factor rows
+constexpr int kBandStageBytes = 45 * 1024;
+constexpr int kBandMaxW = 4096;
+constexpr double kBandMaxBytes = 64.0 * 1024 * 1024 * 1024;
+
+// rank of node i along an axis: identity on a Neumann axis, folded on a
+// periodic one (neighbours i, i+-1 and i+-2 mod N land at most 2 and 4 apart)
+std::vector<int> axis_rank(int N, int per) {
+  std::vector<int> r((size_t)N);
+  for (int i = 0; i < N; ++i) r[(size_t)i] = (!per) ? i : (2 * i < N ? 2 * i : 2 * (N - 1 - i) + 1);
+  return r;
+}
+
+// Sparse row with a handful of entries (K_nu^2 has at most 13 per row).
+struct Row {
+  int col[32];
+  double val[32];
+  int n = 0;
+  void add(int c, double v) {
+    for (int q = 0; q < n; ++q)
+      if (col[q] == c) {
+        val[q] += v;
+        return;
+      }
+    col[n] = c;
+    val[n] = v;
+    ++n;
+  }
+};
+
+// Row a of the 5-point operator sum over faces coef_f (u_a - u_nb): the
+// "plus" face of a node carries fx[a] / fy[a]; its "minus" face is the plus
+// face of the minus neighbour.  Faces past a Neumann end do not exist.
+void five_point_row(const Geom& g, const std::vector<double>& fx, const std::vector<double>& fy, int a,
+                    Row& r) {
+  const int i = a / g.ny, j = a % g.ny;
+  r.n = 0;
+  r.add(a, 0.0);
+  auto face = [&](int nb, double c) {
+    r.add(a, c);
+    r.add(nb, -c);
+  };
+  if (g.actx) {
+    if (g.perx || i < g.nx - 1) face(((i + 1) % g.nx) * g.ny + j, fx[(size_t)a]);
+    if (g.perx || i > 0) {
+      const int im = (i + g.nx - 1) % g.nx;
+      face(im * g.ny + j, fx[(size_t)im * g.ny + j]);
+    }
+  }
+  if (g.pery || j < g.ny - 1) face(i * g.ny + (j + 1) % g.ny, fy[(size_t)a]);
+  if (g.pery || j > 0) {
+    const int jm = (j + g.ny - 1) % g.ny;
+    face(i * g.ny + jm, fy[(size_t)i * g.ny + jm]);
+  }
+}
+
+// In-place banded Cholesky of an SPD matrix in lower column storage
+// A[j (w+1) + (i - j)], 0 <= i - j <= w.  Returns false on a non-positive or
+// non-finite pivot.
+bool band_cholesky(std::vector<double>& A, int S, int w) {
+  const size_t ld = (size_t)w + 1;
+  for (int j = 0; j < S; ++j) {
+    double* cj = &A[(size_t)j * ld];
+    const double d = cj[0];
+    if (!(d > 0.0) || !std::isfinite(d)) return false;
+    const double ljj = std::sqrt(d), inv = 1.0 / ljj;
+    cj[0] = ljj;
+    const int m = std::min(w, S - 1 - j);
+    for (int e = 1; e <= m; ++e) cj[e] *= inv;
+    for (int e1 = 1; e1 <= m; ++e1) {
+      const double lk = cj[e1];
+      if (lk == 0.0) continue;
+      double* ck = &A[(size_t)(j + e1) * ld];
+      for (int e2 = e1; e2 <= m; ++e2) ck[e2 - e1] -= cj[e2] * lk;
+    }
+  }
+  return true;
+}
+
+template <typename T>
+T* upload_vec(const std::vector<T>& h) {
+  T* d = nullptr;
+  if (cudaMalloc(&d, h.size() * sizeof(T)) != cudaSuccess) return nullptr;
+  if (cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return nullptr;
+  }
+  return d;
+}
+
+// padded row length: a multiple of 16 bytes so every row starts 16-byte aligned
+int band_row_words(int w, size_t elt) {
+  const int per16 = (int)(16 / elt);
+  return (w + 1 + per16 - 1) / per16 * per16;
+}
+
+template <typename T>
+int build_factors(const Geom& g, const std::vector<Row>& chat, const std::vector<Row>& lhat,
+                  const std::vector<int>& ipos, const double* lamt, int w, PrecTables* t,
+                  std::string* err) {
+  const int S = g.S, nt = g.nt;
+  const int wp = band_row_words(w, sizeof(T));
+  const size_t per = (size_t)S * wp;
+  std::vector<T> Lc(per * nt, T(0)), Lr(per * nt, T(0));
+  std::vector<int> bad((size_t)nt, 0);
+  auto work = [&](int k0, int k1) {
+    std::vector<double> A((size_t)S * (w + 1));
+    for (int k = k0; k < k1; ++k) {
+      std::fill(A.begin(), A.end(), 0.0);
+      for (int a = 0; a < S; ++a) {
+        const int pa = ipos[(size_t)a];
+        auto put = [&](const Row& r, double scale) {
+          for (int q = 0; q < r.n; ++q) {
+            const int pc = ipos[(size_t)r.col[q]];
+            if (pc < pa) continue;  // lower triangle in column storage: (row pc, col pa), pc >= pa
+            A[(size_t)pa * (w + 1) + (pc - pa)] += scale * r.val[q];
+          }
+        };
+        put(chat[(size_t)a], 1.0);
+        put(lhat[(size_t)a], lamt[k]);
+      }
+      if (!band_cholesky(A, S, w)) {
+        bad[(size_t)k] = 1;
+        continue;
+      }
+      T* lc = Lc.data() + per * k;
+      T* lr = Lr.data() + per * k;
+      for (int j = 0; j < S; ++j) {
+        const double* cj = &A[(size_t)j * (w + 1)];
+        lc[(size_t)j * wp] = (T)(1.0 / cj[0]);
+        lr[(size_t)j * wp] = (T)(1.0 / cj[0]);
+        for (int e = 1; e <= w; ++e) {
+          if (j + e < S) lc[(size_t)j * wp + e] = (T)cj[e];                             // L_{j+e, j}
+          if (j - e >= 0) lr[(size_t)j * wp + e] = (T)A[(size_t)(j - e) * (w + 1) + e];  // L_{j, j-e}
+        }
+      }
+    }
+  };
+  const int nth = std::max(1, std::min(nt, (int)std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int q = 0; q < nth; ++q) pool.emplace_back(work, q * nt / nth, (q + 1) * nt / nth);
+  for (auto& th : pool) th.join();
+  for (int k = 0; k < nt; ++k)
+    if (bad[(size_t)k]) {
+      *err = "viscosity field: a per-frequency system is not positive definite";
+      return MFG_ERR_INVALID_ARG;
+    }
+  T* dc = upload_vec(Lc);
+  T* dr = upload_vec(Lr);
+  if (!dc || !dr) {
+    if (dc) cudaFree(dc);
+    if (dr) cudaFree(dr);
+    *err = "cudaMalloc failed for the banded factors";
+    return MFG_ERR_CUDA;
+  }
+  if constexpr (sizeof(T) == 8) {
+    t->bandc64 = dc;
+    t->bandr64 = dr;
+  } else {
+    t->bandc32 = dc;
+    t->bandr32 = dr;
+  }
+  return MFG_OK;
+}
+
+}  // namespace
+
+int build_band_tables(const mfg_problem& p, const Geom& g, const double* lamt, PrecTables* t,
+                      std::string* err) {
+  const int S = g.S;
+  // node viscosities on the internal (nx, ny) grid: the caller's [Nx][Ny]
+  // array, which for d = 1 is the N values along the internal y axis
+  const double* nu = p.nu_field;
+  std::vector<double> fx((size_t)S, 0.0), fy((size_t)S, 0.0), ux((size_t)S, 0.0), uy((size_t)S, 0.0);
+  for (int i = 0; i < g.nx; ++i)
+    for (int j = 0; j < g.ny; ++j) {
+      const size_t a = (size_t)i * g.ny + j;
+      if (g.actx && (g.perx || i < g.nx - 1)) {
+        const size_t b = (size_t)((i + 1) % g.nx) * g.ny + j;
+        fx[a] = 0.5 * (nu[a] + nu[b]) * g.ax;
+        ux[a] = g.ax;
+      }
+      if (g.pery || j < g.ny - 1) {
+        const size_t b = (size_t)i * g.ny + (j + 1) % g.ny;
+        fy[a] = 0.5 * (nu[a] + nu[b]) * g.ay;
+        uy[a] = g.ay;
+      }
+    }
+  // band order
+  const std::vector<int> rx = axis_rank(g.nx, g.perx), ry = axis_rank(g.ny, g.pery);
+  std::vector<int> ipos((size_t)S);
+  for (int i = 0; i < g.nx; ++i)
+    for (int j = 0; j < g.ny; ++j) ipos[(size_t)i * g.ny + j] = rx[(size_t)i] * g.ny + ry[(size_t)j];
+  // rows of K_nu and K, then C_hat = K_nu^2 + 2K and L_hat = (K_nu + I/dt)/dt
+  std::vector<Row> kv((size_t)S), chat((size_t)S), lhat((size_t)S);
+  for (int a = 0; a < S; ++a) five_point_row(g, fx, fy, a, kv[(size_t)a]);
+  const double idt = g.idt;
+  int w = 0;
+  for (int a = 0; a < S; ++a) {
+    Row k1;
+    five_point_row(g, ux, uy, a, k1);
+    Row& c = chat[(size_t)a];
+    const Row& ra = kv[(size_t)a];
+    for (int q = 0; q < ra.n; ++q) {
+      const Row& rb = kv[(size_t)ra.col[q]];
+      for (int u = 0; u < rb.n; ++u) c.add(rb.col[u], ra.val[q] * rb.val[u]);
+    }
+    for (int q = 0; q < k1.n; ++q) c.add(k1.col[q], 2.0 * k1.val[q]);
+    Row& l = lhat[(size_t)a];
+    for (int q = 0; q < ra.n; ++q) l.add(ra.col[q], ra.val[q] * idt);
+    l.add(a, idt * idt);
+    for (int q = 0; q < c.n; ++q) w = std::max(w, std::abs(ipos[(size_t)c.col[q]] - ipos[(size_t)a]));
+  }
+  w = std::max(w, 1);
+  const size_t elt = p.precision == MFG_FP64 ? 8 : 4;
+  const double bytes = 2.0 * g.nt * (double)S * band_row_words(w, elt) * elt;
+  if (w > kBandMaxW || bytes > kBandMaxBytes) {
+    *err = "viscosity field: banded factors too large (half-bandwidth " + std::to_string(w) +
+           ", " + std::to_string(bytes / 1073741824.0) + " GiB)";
+    return MFG_ERR_UNSUPPORTED;
+  }
+  t->band_w = w;
+  t->kfx = upload_vec(fx);
+  t->kfy = upload_vec(fy);
+  t->band_perm = upload_vec(ipos);
+  if (!t->kfx || !t->kfy || !t->band_perm) {
+    *err = "cudaMalloc failed for the viscosity tables";
+    return MFG_ERR_CUDA;
+  }
+  if (p.precision == MFG_FP64) return build_factors<double>(g, chat, lhat, ipos, lamt, w, t, err);
+  return build_factors<float>(g, chat, lhat, ipos, lamt, w, t, err);
+}
+
+// ---------------------------------------------------------------- device --
+namespace {
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+template <int B>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Time transform of every spatial point: out[k][.] = sum_j V[k][j] in[j][.]
+// (V symmetric and orthonormal, so the same product is forward and inverse).
+// TO_BAND: outputs go to band positions ipos[s]; FROM_BAND: inputs are read
+// from them.  A block holds a strip of 32 points x N_t levels in shared memory;
+// lanes own points, warps own output levels.
+template <typename TI, typename TO, typename T, bool FROM_BAND, bool TO_BAND>
+__global__ void __launch_bounds__(256) k_time_xf(const TI* __restrict__ in, TO* __restrict__ out,
+                                                 const T* __restrict__ V, const int* __restrict__ ipos,
+                                                 int nt, int S, const DevScalars* sc) {
+  if (sc != nullptr && sc->cg_done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* strip = reinterpret_cast<T*>(smraw);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int s = blockIdx.x * 32 + lane;
+  const bool ok = s < S;
+  const int ps = ok ? ipos[s] : 0;
+  const long long src = FROM_BAND ? ps : s, dst = TO_BAND ? ps : s;
+  for (int j = wid; j < nt; j += 8) strip[j * 32 + lane] = ok ? (T)in[(long long)j * S + src] : T(0);
+  __syncthreads();
+  if (!ok) return;
+  for (int k = wid; k < nt; k += 8) {
+    const T* vr = V + (size_t)k * nt;
+    T acc = T(0);
+    for (int j = 0; j < nt; ++j) acc = fma(vr[j], strip[j * 32 + lane], acc);
+    out[(long long)k * S + dst] = (TO)acc;
+  }
+}
+
+// One banded substitution per frequency (blockIdx.x = k), in band order.
+//   forward (BWD = false): L y = b, walking j = 0..S-1 with the column layout
+//     (row j of F: 1/L_jj, then L_{j+1+e, j});
+//   backward (BWD = true): L^T x = y, walking j = S-1..0 with the row layout
+//     (row j of F: 1/L_jj, then L_{j, j-1-e}).
+// Step j: x_j = acc_j / L_jj, then acc_i -= F_j[1+e] x_j for the w entries
+// i = j +- (1+e) still ahead, and the entry w+1 ahead enters the window.  The
+// window keeps entry i at slot i mod (w+2), so a step never writes the slot
+// it reads or the slot it refills.  Factor rows arrive through a ring of
+// kBandRing stages of G rows each (cp.async, 16-byte chunks), with the
+// refill values of each stage (4- or 8-byte copies); cp.async.wait_group only
+// waits for copies already issued, so the pipeline cannot stall for good.
+template <typename T, bool BWD>
+__global__ void __launch_bounds__(1024) k_band_pass(const T* __restrict__ rhs, T* __restrict__ sol,
+                                                    const T* __restrict__ F, int S, int w, int wp, int G,
+                                                    const DevScalars* sc) {
+  if (sc != nullptr && sc->cg_done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* ring = reinterpret_cast<T*>(smraw);               // kBandRing x G x wp
+  T* refill = ring + (size_t)kBandRing * G * wp;       // kBandRing x G
+  T* win = refill + (size_t)kBandRing * G;             // w + 2
+  const int k = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const int W2 = w + 2;
+  const T* Fk = F + (size_t)k * S * wp;
+  const T* bk = rhs + (size_t)k * S;
+  T* xk = sol + (size_t)k * S;
+  const int nst = (S + G - 1) / G;
+  // rows [lo, lo + cnt) of stage st, and the band index of step t
+  auto stage_lo = [&](int st) {
+    if (!BWD) return st * G;
+    return max(0, S - (st + 1) * G);
+  };
+  auto stage_cnt = [&](int st) {
+    const int a = st * G, b = min(S, a + G);
+    return b - a;
+  };
+  auto issue = [&](int st) {
+    if (st < nst) {
+      const int lo = stage_lo(st), cnt = stage_cnt(st);
+      T* dst = ring + (size_t)(st % kBandRing) * G * wp;
+      const char* g0 = reinterpret_cast<const char*>(Fk + (size_t)lo * wp);
+      const int chunks = (int)((size_t)cnt * wp * sizeof(T) / 16);
+      for (int c = tid; c < chunks; c += nth) cp_async16(reinterpret_cast<char*>(dst) + 16 * (size_t)c, g0 + 16 * (size_t)c);
+      if (tid < cnt) {
+        const int t = st * G + tid;
+        const int j = BWD ? S - 1 - t : t;
+        const int r = BWD ? j - w - 1 : j + w + 1;
+        if (r >= 0 && r < S) cp_async_small<sizeof(T)>(refill + (st % kBandRing) * G + tid, bk + r);
+      }
+    }
+    cp_async_commit();
+  };
+  // initial window: the w+1 entries nearest the start
+  for (int e = tid; e <= w && e < S; e += nth) {
+    const int i = BWD ? S - 1 - e : e;
+    win[i % W2] = bk[i];
+  }
+  for (int st = 0; st < kBandRing - 1; ++st) issue(st);
+  int sj = BWD ? (S - 1) % W2 : 0;  // slot of the current entry j
+  for (int st = 0; st < nst; ++st) {
+    cp_async_wait<kBandRing - 2>();
+    __syncthreads();
+    issue(st + kBandRing - 1);
+    const T* rows = ring + (size_t)(st % kBandRing) * G * wp;
+    const T* rv = refill + (st % kBandRing) * G;
+    const int lo = stage_lo(st), cnt = stage_cnt(st);
+    for (int u = 0; u < cnt; ++u) {
+      const int t = st * G + u;
+      const int j = BWD ? S - 1 - t : t;
+      const T* f = rows + (size_t)(j - lo) * wp;
+      const T xj = win[sj] * f[0];
+      for (int e = tid; e < w; e += nth) {
+        const int i = BWD ? j - 1 - e : j + 1 + e;
+        if (i >= 0 && i < S) {
+          int sl = BWD ? sj - 1 - e : sj + 1 + e;
+          sl += (sl < 0) ? W2 : ((sl >= W2) ? -W2 : 0);
+          win[sl] -= f[1 + e] * xj;
+        }
+      }
+      if (tid == 0) {
+        xk[j] = xj;
+        const int r = BWD ? j - w - 1 : j + w + 1;
+        if (r >= 0 && r < S) {
+          const int sl = BWD ? (sj + 1 == W2 ? 0 : sj + 1) : (sj == 0 ? W2 - 1 : sj - 1);
+          win[sl] = rv[u];
+        }
+      }
+      __syncthreads();
+      sj = BWD ? (sj == 0 ? W2 - 1 : sj - 1) : (sj + 1 == W2 ? 0 : sj + 1);
+    }
+  }
+  cp_async_wait<0>();
+}
+
+struct BandShape {
+  int wp, G, threads;
+  size_t smem;
+};
+
+template <typename T>
+BandShape band_shape(int w) {
+  BandShape b;
+  b.wp = band_row_words(w, sizeof(T));
+  b.G = std::max(1, std::min(16, kBandStageBytes / (int)(b.wp * sizeof(T))));
+  b.threads = std::min(1024, (w + 31) / 32 * 32);
+  b.smem = sizeof(T) * ((size_t)kBandRing * b.G * b.wp + (size_t)kBandRing * b.G + (size_t)w + 2);
+  return b;
+}
+
+template <typename T>
+void precond_band_typed(const Geom& g, const PrecTables& t, const T* V, const T* Lc, const T* Lr,
+                        const double* r, double* z, T* w0, T* w1, const DevScalars* sc, cudaStream_t s) {
+  const int S = g.S, nt = g.nt, w = t.band_w;
+  const size_t tsm = sizeof(T) * (size_t)nt * 32;
+  const int tb = (S + 31) / 32;
+  k_time_xf<double, T, T, false, true><<<tb, 256, tsm, s>>>(r, w0, V, t.band_perm, nt, S, sc);
+  const BandShape b = band_shape<T>(w);
+  k_band_pass<T, false><<<nt, b.threads, b.smem, s>>>(w0, w1, Lc, S, w, b.wp, b.G, sc);
+  k_band_pass<T, true><<<nt, b.threads, b.smem, s>>>(w1, w0, Lr, S, w, b.wp, b.G, sc);
+  k_time_xf<T, double, T, true, false><<<tb, 256, tsm, s>>>(w0, z, V, t.band_perm, nt, S, sc);
+}
+
+}  // namespace
+
+// Largest dynamic shared memory the band kernels ask for (half-bandwidth up
+// to kBandMaxW); called once per device before any launch or capture.
+int band_configure() {
+  int bad = 0;
+  const size_t s64 = std::max(band_shape<double>(kBandMaxW).smem, band_shape<double>(8).smem);
+  const size_t s32 = std::max(band_shape<float>(kBandMaxW).smem, band_shape<float>(8).smem);
+  size_t m64 = 0, m32 = 0;
+  for (int w = 1; w <= kBandMaxW; w = w < 64 ? w + 1 : w + 32) {
+    m64 = std::max(m64, band_shape<double>(w).smem);
+    m32 = std::max(m32, band_shape<float>(w).smem);
+  }
+  m64 = std::max(m64, s64);
+  m32 = std::max(m32, s32);
+  bad |= cudaFuncSetAttribute(k_band_pass<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m64) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(k_band_pass<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m64) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(k_band_pass<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m32) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(k_band_pass<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m32) != cudaSuccess;
+  const int t64 = (int)(sizeof(double) * kMaxNt * 32), t32 = (int)(sizeof(float) * kMaxNt * 32);
+  bad |= cudaFuncSetAttribute(k_time_xf<double, double, double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, t64) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(k_time_xf<double, double, double, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, t64) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(k_time_xf<double, float, float, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, t32) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(k_time_xf<float, double, float, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, t32) != cudaSuccess;
+  return bad ? MFG_ERR_CUDA : MFG_OK;
+}
+
+void launch_precond_band(const Geom& g, const PrecTables& t, int precision, const double* r, double* z,
+                         double* work64, float* work32, const DevScalars* sc, cudaStream_t s) {
+  if (precision == MFG_FP64)
+    precond_band_typed<double>(g, t, t.Vt64, t.bandc64, t.bandr64, r, z, work64, work64 + g.n, sc, s);
+  else
+    precond_band_typed<float>(g, t, t.Vt32, t.bandc32, t.bandr32, r, z, work32, work32 + g.n, sc, s);
+}
+
+}  // namespace mfg

@@ -202,6 +202,13 @@ int build_prec_tables(const mfg_problem& p, const Geom& g, PrecTables* t, std::s
     free_prec_tables(t);
     return MFG_ERR_CUDA;
   }
+  if (p.nu_field != nullptr) {
+    const int rc = build_band_tables(p, g, lt.data(), t, err);
+    if (rc != MFG_OK) {
+      free_prec_tables(t);
+      return rc;
+    }
+  }
   return MFG_OK;
 }
 
@@ -209,7 +216,8 @@ void free_prec_tables(PrecTables* t) {
   void* ptrs[] = {t->Hx64, t->Hy64, t->Vt64, t->lamt64, t->L1_64, t->L2_64, t->Hx32, t->Hy32,
                   t->Vt32, t->lamt32, t->L1_32, t->L2_32, t->twx64, t->twx32, t->dctx64, t->dctx32,
                   t->twy64, t->twy32, t->dcty64, t->dcty32, t->thc64, t->thd64, t->tho64,
-                  t->thc32, t->thd32, t->tho32};
+                  t->thc32, t->thd32, t->tho32, t->kfx, t->kfy, t->band_perm, t->bandc64,
+                  t->bandr64, t->bandc32, t->bandr32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   *t = PrecTables{};
@@ -621,6 +629,12 @@ static void precond_typed(const Geom& g, const T* Hx, const T* Hy, const T* V, c
 void launch_precond(const Geom& g, const PrecTables& t, int precision, const double* r, double* z,
                     double* work64, float* work32, const DevScalars* sc, cudaStream_t s,
                     const PcgDot* dot, const PcgZr* zr) {
+  if (t.band_w > 0) {  // viscosity field: time transforms around banded per-frequency solves
+    if (zr) launch_update_zr(g.n, zr->z, zr->r, zr->p, zr->q, zr->partials, zr->sc, s, g.vec_blocks);
+    launch_precond_band(g, t, precision, r, z, work64, work32, sc, s);
+    if (dot) launch_dot_beta(g.n, dot->r, z, dot->q, dot->flex, dot->partials, dot->sc, s, g.vec_blocks);
+    return;
+  }
   if (precision == MFG_MIXED || precision == MFG_MIXED_DF || precision == MFG_MIXED_TC)
     precond_typed<float>(g, t.Hx32, t.Hy32, t.Vt32, t.lamt32, t.L1_32, t.L2_32, t.twx32, t.dctx32,
                          t.twy32, t.dcty32, t.thc32, t.thd32, t.tho32, r, z, work32, work32 + g.n,
@@ -631,10 +645,11 @@ void launch_precond(const Geom& g, const PrecTables& t, int precision, const dou
                           sc, s, dot, zr);
 }
 
-int precond_kernel_count(const Geom& g) { return g.nx > 1 ? 5 : 3; }
+int precond_kernel_count(const Geom& g) { return g.kfy != nullptr ? 4 : (g.nx > 1 ? 5 : 3); }
 
 // Kernels of a preconditioner apply that also runs the PCG update and dot products.
 int precond_step_kernel_count(const Geom& g, const PrecTables& t) {
+  if (t.band_w > 0) return 4 + 2;
   const bool fused = g.fft_y && t.twy32 != nullptr && fft_supported(g.ny);
   return precond_kernel_count(g) + (fused ? 0 : 2);
 }
@@ -654,6 +669,7 @@ int precond_configure() {
   MFG_TF_ATTR(double, 32) MFG_TF_ATTR(double, 64) MFG_TF_ATTR(double, 128)
 #undef MFG_TF_ATTR
   bad |= fft_configure() != MFG_OK;
+  bad |= band_configure() != MFG_OK;
   bad |= time_tc_configure() != MFG_OK;
   return bad ? MFG_ERR_CUDA : MFG_OK;
 }

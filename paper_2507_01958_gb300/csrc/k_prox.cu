@@ -248,8 +248,10 @@ __device__ __forceinline__ void prox_cell(double mbar, const double (&wbar)[NW],
 //   K z = ax ((z - zE) - (zW - z)) + ay ((z - zN) - (zS - z));
 // on a Neumann axis the neighbour index of an end point is the point itself,
 // so the difference across the end (a flux slot of Sec. 4.3 that does not
-// exist) is zero and K takes its one-sided form.
-template <int ACTX, bool GENQ>
+// exist) is zero and K takes its one-sided form.  VN (viscosity field): nu K z
+// becomes K_nu z = kf_yp dyp - kf_ym dym (+ x terms), the face coefficients of
+// Geom::kfx / kfy.
+template <int ACTX, bool GENQ, bool VN>
 __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const double* __restrict__ z,
                                                       double* __restrict__ y, double* __restrict__ ybar,
                                                       const double* __restrict__ V,
@@ -279,13 +281,17 @@ __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const dou
     const double zc = z[e];
     if (Az != nullptr) Az[e] -= rfin[e];  // AAt z_{l+1} = b - r_final (stop reference)
     const double dyp = zc - z[rowi + jp], dym = z[rowi + jm] - zc;
-    double Kz = g.ay * (dyp - dym);
+    const long long f0 = (long long)i * g.ny;
+    double Kz = VN ? fma(g.kfy[f0 + j], dyp, -g.kfy[f0 + jm] * dym) : g.ay * (dyp - dym);
     double d[NW];
     if (ACTX) {
       const int im = i == 0 ? (g.perx ? g.nx - 1 : 0) : i - 1;
       const int ip = i == g.nx - 1 ? (g.perx ? 0 : g.nx - 1) : i + 1;
       const double dxp = zc - z[base + (long long)ip * g.ny + j], dxm = z[base + (long long)im * g.ny + j] - zc;
-      Kz = fma(g.ax, dxp - dxm, Kz);
+      if (VN)
+        Kz = fma(g.kfx[f0 + j], dxp, fma(-g.kfx[(long long)im * g.ny + j], dxm, Kz));
+      else
+        Kz = fma(g.ax, dxp - dxm, Kz);
       d[0] = dxp; d[1] = dxm; d[2] = dyp; d[3] = dym;
     } else {
       d[0] = dyp; d[1] = dym;
@@ -293,7 +299,7 @@ __global__ void __launch_bounds__(kThreads) k_prox_cp(Geom g, Coef cf, const dou
     const double zn = (k + 1 < g.nt) ? z[e + g.S] : 0.0;
     // primal step y - tau x, x_m = nu K z + (z - z_next)/dt, x_w = d / dx
     const double m_old = y[e];
-    const double mbar = fma(-t_nu, Kz, fma(-t_idt, zc - zn, m_old));
+    const double mbar = fma(VN ? -tau : -t_nu, Kz, fma(-t_idt, zc - zn, m_old));
     double w_old[NW], wbar[NW], w_new[NW];
 #pragma unroll
     for (int q = 0; q < NW; ++q) {
@@ -387,18 +393,19 @@ void launch_prox_cp(const Geom& g, const Coef& cf, const double* z, double* y, d
                     cudaGraphConditionalHandle h, int use_handle, cudaStream_t s, double* Az,
                     const double* rfin) {
   const int nb = red_blocks(g.n, g.vec_blocks);
-  // the general-q' root finder is its own instantiation, so the q' = 2 kernel
-  // keeps its registers
-  if (cf.qprime != 2.0) {
-    if (g.actx)
-      k_prox_cp<1, true><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle, Az, rfin);
-    else
-      k_prox_cp<0, true><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle, Az, rfin);
-  } else if (g.actx) {
-    k_prox_cp<1, false><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle, Az, rfin);
+  // the general-q' root finder and the viscosity field are their own
+  // instantiations, so the q' = 2, constant-nu kernel keeps its registers
+#define MFG_PROX_CP(A, Q, N) \
+  k_prox_cp<A, Q, N><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle, Az, rfin)
+  const bool gq = cf.qprime != 2.0, vn = g.kfy != nullptr;
+  if (g.actx) {
+    if (gq) { if (vn) MFG_PROX_CP(1, true, true); else MFG_PROX_CP(1, true, false); }
+    else    { if (vn) MFG_PROX_CP(1, false, true); else MFG_PROX_CP(1, false, false); }
   } else {
-    k_prox_cp<0, false><<<nb, kThreads, 0, s>>>(g, cf, z, y, ybar, V, W, partials, sc, h, use_handle, Az, rfin);
+    if (gq) { if (vn) MFG_PROX_CP(0, true, true); else MFG_PROX_CP(0, true, false); }
+    else    { if (vn) MFG_PROX_CP(0, false, true); else MFG_PROX_CP(0, false, false); }
   }
+#undef MFG_PROX_CP
 }
 
 void launch_prox_plain(const Geom& g, const Coef& cf, double tau, const double* v, double* y,

@@ -56,7 +56,10 @@ __device__ __forceinline__ int wrap_or_neg(int i, int N, int per) {
 //         alpha = rz/(pdot.r).
 // mode 3: adjoint right-hand side r = C v; reduces ||r||^2, resets the PCG
 //         state with the fixed tolerance.
-template <int ACTX>
+// VN (viscosity field): nu K m becomes K_nu m = sum over the node's faces of
+// kf (m - m_nb), kf the face coefficient of Geom::kfx / kfy; at a Neumann end
+// the neighbour index is the node itself, so the missing face adds nothing.
+template <int ACTX, bool VN>
 __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __restrict__ v,
                                                       double* __restrict__ r, double alpha,
                                                       const double* __restrict__ m0,
@@ -92,15 +95,26 @@ __global__ void __launch_bounds__(kThreads) k_apply_C(Geom g, const double* __re
     const double sy = ((by.hp ? wy1[e] : 0.0) - (by.hm ? wy1[rowi + by.im] : 0.0)) +
                       ((by.hp ? wy2[rowi + by.ip] : 0.0) - (by.hm ? wy2[e] : 0.0));
     double val;
+    double kvm = 0.0;  // K_nu m (VN)
+    if (VN) {
+      const long long f = (long long)i * g.ny;
+      kvm = fma(g.kfy[f + j], mc - m[rowi + by.ip], g.kfy[f + by.im] * (mc - m[rowi + by.im]));
+    }
     if (ACTX) {
       const Nb bx = nbr(i, g.nx, g.perx);
       const long long em = base + (long long)bx.im * g.ny + j, ep = base + (long long)bx.ip * g.ny + j;
       t1 = fma(kx, m[em] + m[ep], t1);
       const double sx = ((bx.hp ? wx1[e] : 0.0) - (bx.hm ? wx1[em] : 0.0)) +
                         ((bx.hp ? wx2[ep] : 0.0) - (bx.hm ? wx2[e] : 0.0));
-      val = fma(aix, sx, fma(aiy, sy, fma(kc, mc, -t1)));
+      if (VN) {
+        kvm = fma(g.kfx[(long long)i * g.ny + j], mc - m[ep], kvm);
+        kvm = fma(g.kfx[(long long)bx.im * g.ny + j], mc - m[em], kvm);
+        val = fma(aix, sx, fma(aiy, sy, alpha * kvm));
+      } else {
+        val = fma(aix, sx, fma(aiy, sy, fma(kc, mc, -t1)));
+      }
     } else {
-      val = fma(aiy, sy, fma(kc, mc, -t1));
+      val = VN ? fma(aiy, sy, alpha * kvm) : fma(aiy, sy, fma(kc, mc, -t1));
     }
     const double mprev = k >= 1 ? m[e - g.S] : (m0 != nullptr ? m0[(long long)i * g.ny + j] : 0.0);
     val = fma(aidt, mc - mprev, val);
@@ -155,15 +169,21 @@ void launch_apply_C(const Geom& g, const double* v, double* r, double alpha, con
                     double* partials, DevScalars* sc, int mode, cudaStream_t s, const double* pdot,
                     double* Az) {
   const int nb = red_blocks(g.n, g.vec_blocks);
-  if (g.actx)
-    k_apply_C<1><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, pdot, partials, sc, mode, Az);
+  const bool vn = g.kfy != nullptr;
+  if (g.actx && vn)
+    k_apply_C<1, true><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, pdot, partials, sc, mode, Az);
+  else if (g.actx)
+    k_apply_C<1, false><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, pdot, partials, sc, mode, Az);
+  else if (vn)
+    k_apply_C<0, true><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, pdot, partials, sc, mode, Az);
   else
-    k_apply_C<0><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, pdot, partials, sc, mode, Az);
+    k_apply_C<0, false><<<nb, kThreads, 0, s>>>(g, v, r, alpha, m0, pdot, partials, sc, mode, Az);
 }
 
 // ----------------------------------------------------------------- C^T p --
 // x_m^k = L p^k - p^{k+1}/dt (p^{N_t} := 0),  x_w^k = B^T p^k = -D_h p^k.
-template <int ACTX>
+// VN: L = K_nu + I/dt with the face coefficients of Geom::kfx / kfy.
+template <int ACTX, bool VN>
 __global__ void __launch_bounds__(kThreads) k_apply_Ct(Geom g, const double* __restrict__ p,
                                                        double* __restrict__ x) {
   const long long n = g.n;
@@ -183,27 +203,37 @@ __global__ void __launch_bounds__(kThreads) k_apply_Ct(Geom g, const double* __r
     const Nb by = nbr(j, g.ny, g.pery);
     const double pc = p[e];
     const double pjm = p[rowi + by.im], pjp = p[rowi + by.ip];
-    double Kp = g.ay * ((by.hm ? pc - pjm : 0.0) + (by.hp ? pc - pjp : 0.0));
+    const long long f = (long long)i * g.ny;
+    double Kp = VN ? fma(g.kfy[f + j], pc - pjp, g.kfy[f + by.im] * (pc - pjm))
+                   : g.ay * ((by.hm ? pc - pjm : 0.0) + (by.hp ? pc - pjp : 0.0));
     xy1[e] = by.hp ? (pc - pjp) * g.idy : 0.0;
     xy2[e] = by.hm ? (pjm - pc) * g.idy : 0.0;
     if (ACTX) {
       const Nb bx = nbr(i, g.nx, g.perx);
       const double pim = p[base + (long long)bx.im * g.ny + j], pip = p[base + (long long)bx.ip * g.ny + j];
-      Kp += g.ax * ((bx.hm ? pc - pim : 0.0) + (bx.hp ? pc - pip : 0.0));
+      if (VN)
+        Kp = fma(g.kfx[f + j], pc - pip, fma(g.kfx[(long long)bx.im * g.ny + j], pc - pim, Kp));
+      else
+        Kp += g.ax * ((bx.hm ? pc - pim : 0.0) + (bx.hp ? pc - pip : 0.0));
       xx1[e] = bx.hp ? (pc - pip) * g.idx : 0.0;
       xx2[e] = bx.hm ? (pim - pc) * g.idx : 0.0;
     }
     const double pn = (k + 1 < g.nt) ? p[e + g.S] : 0.0;
-    xm[e] = g.nu * Kp + (pc - pn) * g.idt;
+    xm[e] = (VN ? Kp : g.nu * Kp) + (pc - pn) * g.idt;
   }
 }
 
 void launch_apply_Ct(const Geom& g, const double* p, double* x, cudaStream_t s) {
   const int nb = red_blocks(g.n, g.vec_blocks);
-  if (g.actx)
-    k_apply_Ct<1><<<nb, kThreads, 0, s>>>(g, p, x);
+  const bool vn = g.kfy != nullptr;
+  if (g.actx && vn)
+    k_apply_Ct<1, true><<<nb, kThreads, 0, s>>>(g, p, x);
+  else if (g.actx)
+    k_apply_Ct<1, false><<<nb, kThreads, 0, s>>>(g, p, x);
+  else if (vn)
+    k_apply_Ct<0, true><<<nb, kThreads, 0, s>>>(g, p, x);
   else
-    k_apply_Ct<0><<<nb, kThreads, 0, s>>>(g, p, x);
+    k_apply_Ct<0, false><<<nb, kThreads, 0, s>>>(g, p, x);
 }
 
 // ---------------------------------------------------------------- C C^T p --
@@ -231,13 +261,17 @@ constexpr int AJ = 32, AI = 8;  // block = AJ x AI columns
 struct AatCoef {
   double ax, ay, cK, ndt;      // pass 1
   double c1, c2, c4, idt2;     // pass 2
+  double dt, idt;              // viscosity field (VN)
 };
 
 AatCoef aat_coef(const Geom& g) {
   const double ax = g.actx ? g.ax : 0.0, ay = g.ay, cK = 2.0 * (ax + ay);
   const double dt = 1.0 / g.idt, idt2 = g.idt * g.idt;
-  return AatCoef{ax, ay, cK, g.nu * dt, g.nu * ay * g.idt, g.nu * ax * g.idt, g.nu * cK * g.idt + idt2, idt2};
+  return AatCoef{ax, ay, cK, g.nu * dt, g.nu * ay * g.idt, g.nu * ax * g.idt, g.nu * cK * g.idt + idt2, idt2,
+                 dt, g.idt};
 }
+
+
 
 int aat2_chunk(const Geom& g) {
   const long long cols = (long long)((g.ny + AJ - 1) / AJ) * ((g.nx + AI - 1) / AI);
@@ -267,7 +301,26 @@ __device__ __forceinline__ Cols aat_cols(const Geom& g, int i, int j) {
   return c;
 }
 
-template <int ACTX>
+// Viscosity field (VN): with L = K_nu + I/dt the two passes read
+//   pass 1:  kp = K p,  X = dt K_nu p + p^k - p^{k+1}
+//   pass 2:  q = (K_nu X)/dt + (X - X^{k-1})/dt^2 + 2 kp,
+// K_nu u = sum over the node's faces of kf (u - u_nb); the four face
+// coefficients of a column are loaded once, before its march over the planes.
+struct FaceCoef {
+  double yp, ym, xp, xm;
+};
+
+__device__ __forceinline__ FaceCoef face_coef(const Geom& g, int i, int j, const Cols& nb, double scale) {
+  FaceCoef f;
+  const long long row = (long long)i * g.ny;
+  f.yp = g.kfy[row + j] * scale;
+  f.ym = g.kfy[row + nb.jm] * scale;
+  f.xp = g.actx ? g.kfx[row + j] * scale : 0.0;
+  f.xm = g.actx ? g.kfx[(long long)nb.im * g.ny + j] * scale : 0.0;
+  return f;
+}
+
+template <int ACTX, bool VN>
 __global__ void __launch_bounds__(AJ * AI) k_aat_x(Geom g, AatCoef a, int kc, const double* __restrict__ p,
                                                    double* __restrict__ X, double* __restrict__ KP,
                                                    const DevScalars* sc, int mode) {
@@ -277,14 +330,28 @@ __global__ void __launch_bounds__(AJ * AI) k_aat_x(Geom g, AatCoef a, int kc, co
   const int k0 = blockIdx.z * kc, k1 = min(g.nt, k0 + kc);
   const Cols nb = aat_cols(g, i, j);
   const long long row = (long long)i * g.ny;
+  FaceCoef fc{0.0, 0.0, 0.0, 0.0};
+  if (VN) fc = face_coef(g, i, j, nb, a.dt);
   long long base = (long long)k0 * g.S;
   double c = p[base + row + j];
   for (int k = k0; k < k1; ++k) {
     const double pn = (k + 1 < g.nt) ? p[base + g.S + row + j] : 0.0;
-    double t = a.ay * (p[base + row + nb.jm] + p[base + row + nb.jp]);
-    if (ACTX) t = fma(a.ax, p[base + (long long)nb.im * g.ny + j] + p[base + (long long)nb.ip * g.ny + j], t);
+    const double pS = p[base + row + nb.jm], pN = p[base + row + nb.jp];
+    double t = a.ay * (pS + pN);
+    double pW = 0.0, pE = 0.0;
+    if (ACTX) {
+      pW = p[base + (long long)nb.im * g.ny + j];
+      pE = p[base + (long long)nb.ip * g.ny + j];
+      t = fma(a.ax, pW + pE, t);
+    }
     const double kp = fma(a.cK, c, -t);
-    X[base + row + j] = fma(a.ndt, kp, c - pn);
+    if (VN) {
+      double kv = fma(fc.yp, c - pN, fc.ym * (c - pS));  // dt K_nu p
+      if (ACTX) kv = fma(fc.xp, c - pE, fma(fc.xm, c - pW, kv));
+      X[base + row + j] = kv + (c - pn);
+    } else {
+      X[base + row + j] = fma(a.ndt, kp, c - pn);
+    }
     KP[base + row + j] = kp;
     c = pn;
     base += g.S;
@@ -293,9 +360,9 @@ __global__ void __launch_bounds__(AJ * AI) k_aat_x(Geom g, AatCoef a, int kc, co
 
 // mode 0: q = AAt p.  mode 1 (PCG step): also reduces p.q and sets
 // alpha = rz/(p.q) in the device scalars.
-template <int ACTX>
+template <int ACTX, bool VN>
 // 2-D: capped at 64 registers (four 256-thread blocks per SM) to hide the load latency
-__global__ void __launch_bounds__(AJ * AI, ACTX ? 4 : 3) k_aat_q(Geom g, AatCoef a, int kc, const double* __restrict__ X,
+__global__ void __launch_bounds__(AJ * AI, (ACTX && !VN) ? 4 : 3) k_aat_q(Geom g, AatCoef a, int kc, const double* __restrict__ X,
                                                    const double* __restrict__ KP, const double* __restrict__ p,
                                                    double* __restrict__ q, double* partials, DevScalars* sc,
                                                    int mode) {
@@ -306,15 +373,28 @@ __global__ void __launch_bounds__(AJ * AI, ACTX ? 4 : 3) k_aat_q(Geom g, AatCoef
     const int k0 = blockIdx.z * kc, k1 = min(g.nt, k0 + kc);
     const Cols nb = aat_cols(g, i, j);
     const long long row = (long long)i * g.ny;
+    FaceCoef fc{0.0, 0.0, 0.0, 0.0};
+    if (VN) fc = face_coef(g, i, j, nb, a.idt);
     long long base = (long long)k0 * g.S;
     double xprev = k0 > 0 ? X[base - g.S + row + j] : 0.0;
     for (int k = k0; k < k1; ++k) {
       const double xc = X[base + row + j];
-      double t = a.c1 * (X[base + row + nb.jm] + X[base + row + nb.jp]);
-      if (ACTX) t = fma(a.c2, X[base + (long long)nb.im * g.ny + j] + X[base + (long long)nb.ip * g.ny + j], t);
-      t = fma(a.idt2, xprev, t);
-      t = fma(-2.0, KP[base + row + j], t);
-      const double qv = fma(a.c4, xc, -t);
+      double qv;
+      if (VN) {
+        const double xS = X[base + row + nb.jm], xN = X[base + row + nb.jp];
+        double kv = fma(fc.yp, xc - xN, fc.ym * (xc - xS));  // K_nu X / dt
+        if (ACTX) {
+          const double xW = X[base + (long long)nb.im * g.ny + j], xE = X[base + (long long)nb.ip * g.ny + j];
+          kv = fma(fc.xp, xc - xE, fma(fc.xm, xc - xW, kv));
+        }
+        qv = fma(2.0, KP[base + row + j], fma(a.idt2, xc - xprev, kv));
+      } else {
+        double t = a.c1 * (X[base + row + nb.jm] + X[base + row + nb.jp]);
+        if (ACTX) t = fma(a.c2, X[base + (long long)nb.im * g.ny + j] + X[base + (long long)nb.ip * g.ny + j], t);
+        t = fma(a.idt2, xprev, t);
+        t = fma(-2.0, KP[base + row + j], t);
+        qv = fma(a.c4, xc, -t);
+      }
       q[base + row + j] = qv;
       if (mode == 1) acc = fma(qv, p[base + row + j], acc);
       xprev = xc;
@@ -435,7 +515,7 @@ void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, doub
   const AatCoef a = aat_coef(g);
   const int kc = aat2_chunk(g);
   const dim3 grid = aat2_grid(g, kc), block(AJ, AI);
-  if (df64) {
+  if (df64 && g.kfy == nullptr) {  // a viscosity field takes the FP64 stencil
     df* X = reinterpret_cast<df*>(scratch);
     df* KP = X + g.n;
     if (g.actx) {
@@ -449,12 +529,19 @@ void launch_AAt(const Geom& g, const double* p, double* q, double* scratch, doub
   }
   double* X = scratch;
   double* KP = scratch + g.n;
-  if (g.actx) {
-    k_aat_x<1><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
-    k_aat_q<1><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
+  const bool vn = g.kfy != nullptr;
+  if (g.actx && vn) {
+    k_aat_x<1, true><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
+    k_aat_q<1, true><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
+  } else if (g.actx) {
+    k_aat_x<1, false><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
+    k_aat_q<1, false><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
+  } else if (vn) {
+    k_aat_x<0, true><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
+    k_aat_q<0, true><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
   } else {
-    k_aat_x<0><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
-    k_aat_q<0><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
+    k_aat_x<0, false><<<grid, block, 0, s>>>(g, a, kc, p, X, KP, sc, mode);
+    k_aat_q<0, false><<<grid, block, 0, s>>>(g, a, kc, X, KP, p, q, partials, sc, mode);
   }
 }
 

@@ -100,6 +100,14 @@ int validate_problem(const mfg_problem& p, int idx) {
                      "precision must be MFG_FP64, MFG_MIXED, MFG_MIXED_DF or MFG_MIXED_TC" + at);
   const double nxy = (double)p.n[0] * (p.dim == 2 ? p.n[1] : 1);
   if (nxy * p.nt > 4.0e9) return set_error(MFG_ERR_INVALID_ARG, "instance too large" + at);
+  if (p.nu_field != nullptr) {
+    if (p.l == 0)
+      return set_error(MFG_ERR_UNSUPPORTED, "a viscosity field needs l = 1 or 2 (the exact time solve is per Laplacian mode)" + at);
+    const long long cnt = (long long)nxy;
+    for (long long a = 0; a < cnt; ++a)
+      if (!(p.nu_field[a] >= 0.0) || !std::isfinite(p.nu_field[a]))
+        return set_error(MFG_ERR_INVALID_ARG, "viscosity field values must be finite and >= 0" + at);
+  }
   return MFG_OK;
 }
 
@@ -343,9 +351,9 @@ int solve_eager(mfg_plan_t pl, const double* m0, const double* V, const double* 
 
 // ------------------------------------------------------------- autotuner --
 // Launch choices per instance shape (grid, N_t, boundary conditions,
-// precision, time solve), measured once per process: a later plan with the
+// precision, time solve, viscosity field or not), measured once per process: a later plan with the
 // same shape takes the cached choice without timing again.
-using TuneKey = std::array<int, 8>;
+using TuneKey = std::array<int, 9>;
 struct TuneVal {
   int vec_blocks, aat_want, time_simt, fft_x, fft_y;
   double precond_us, aat_us;
@@ -355,7 +363,7 @@ std::map<TuneKey, TuneVal> g_tune_cache;
 
 TuneKey tune_key(const Inst& in) {
   return TuneKey{in.g.nx, in.g.ny, in.g.nt, in.g.perx, in.g.pery, in.p.precision, in.p.l == 0 ? 1 : 0,
-                 in.g.actx};
+                 in.g.actx, in.g.kfy != nullptr ? 1 : 0};
 }
 
 // Fills a device buffer with a positive, finite pattern (bytes 0x3F), so that
@@ -609,6 +617,11 @@ int mfg_plan(const mfg_problem* probs, int batch, mfg_plan_t* out) {
     std::string err;
     int rc = build_prec_tables(in.p, in.g, &in.tabs, &err);
     if (rc != MFG_OK) return bail(rc, err);
+    // a viscosity field lives on in the plan's face coefficients and factors;
+    // the caller's array is not retained
+    in.g.kfx = in.tabs.kfx;
+    in.g.kfy = in.tabs.kfy;
+    in.p.nu_field = nullptr;
     const size_t n = (size_t)in.g.n;
     // partial sums for the largest grids any launch choice may use
     Geom gmax = in.g;
@@ -790,6 +803,8 @@ int mfg_adjoint(mfg_plan_t pl, int b, const double* y, const double* z, const do
   Inst& in = pl->inst[b];
   if (in.p.qprime != 2.0)
     return fail(MFG_ERR_UNSUPPORTED, "the adjoint is built for the quadratic Hamiltonian (q' = 2) only");
+  if (pl->inst[b].g.kfy != nullptr)
+    return fail(MFG_ERR_UNSUPPORTED, "the adjoint is built for a constant viscosity only");
   const Geom& g = in.g;
   const size_t n = (size_t)g.n;
   if (!in.adj_t) {

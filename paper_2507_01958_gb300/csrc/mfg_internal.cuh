@@ -39,6 +39,13 @@ struct Geom {
   int aat_want;     // target block count of the AAt stencil launch
   int time_simt;    // 1: time pass on the CUDA cores even where the tensor-core pass applies
   int fft_x, fft_y; // 1: FFT spatial pass where the axis length allows it; 0: dense pass
+  // Viscosity field (mfg_problem::nu_field): per node, the coefficient of its
+  // "plus" face on each axis, nu_face * ax (kfx) and nu_face * ay (kfy), face i
+  // joining nodes i and i+1 (wrapped on a periodic axis, 0 past a Neumann end);
+  // the "minus" face of a node is the plus face of its minus neighbour.  Null
+  // for a constant nu.  Device arrays of S doubles owned by the PrecTables.
+  const double* kfx = nullptr;
+  const double* kfy = nullptr;
 };
 
 // Coefficients of f_eff(m) = a m + b m^2 + c(x) (Sec. 2 calF).
@@ -122,6 +129,18 @@ struct PrecTables {
   // the off-diagonal per mode (S); null otherwise.
   double *thc64 = nullptr, *thd64 = nullptr, *tho64 = nullptr;
   float *thc32 = nullptr, *thd32 = nullptr, *tho32 = nullptr;
+  // Viscosity field: face coefficients (Geom::kfx, kfy) and the banded Cholesky
+  // factors of the per-frequency systems (k_band.cu); null otherwise.
+  double *kfx = nullptr, *kfy = nullptr;
+  int band_w = 0;                 // half-bandwidth w of the factors
+  int* band_perm = nullptr;       // band position -> plane index (S ints)
+  // Factor of frequency k in two layouts of S (w+1) words each, at offset
+  // k S (w+1): by columns (Lc[j(w+1)] = 1/L_jj, Lc[j(w+1)+1+e] = L_{j+1+e, j})
+  // and by rows (Lr[j(w+1)] = 1/L_jj, Lr[j(w+1)+1+e] = L_{j, j-1-e}); zero
+  // outside the matrix.  One precision is allocated: FP64 for MFG_FP64, FP32
+  // otherwise.
+  double *bandc64 = nullptr, *bandr64 = nullptr;
+  float *bandc32 = nullptr, *bandr32 = nullptr;
 };
 // Tensor-core time pass (MFG_MIXED_TC), for N_t in {32, 64, 128}.
 bool time_tc_supported(int nt);
@@ -159,6 +178,14 @@ void launch_precond(const Geom& g, const PrecTables& t, int precision, const dou
                     const PcgDot* dot = nullptr, const PcgZr* zr = nullptr);
 int precond_kernel_count(const Geom& g);
 int precond_step_kernel_count(const Geom& g, const PrecTables& t);
+// Viscosity field (k_band.cu): face coefficients and the banded factors of the
+// per-frequency systems, built on the host in FP64 (lamt: the time
+// eigenvalues); the preconditioner apply through them.
+int build_band_tables(const mfg_problem& p, const Geom& g, const double* lamt, PrecTables* t,
+                      std::string* err);
+void launch_precond_band(const Geom& g, const PrecTables& t, int precision, const double* r, double* z,
+                         double* work64, float* work32, const DevScalars* sc, cudaStream_t s);
+int band_configure();
 int precond_configure();
 
 // FFT spatial passes (k_fft.cu).

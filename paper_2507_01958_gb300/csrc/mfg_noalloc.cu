@@ -169,6 +169,8 @@ extern "C" int mfg_apply_precond_noalloc(const mfg_problem* p, const double* r, 
   if (rc != MFG_OK) return rc;
   if (p->l == 0)
     return set_error(MFG_ERR_UNSUPPORTED, "mfg_apply_precond_noalloc: l = 0 needs plan-built factors");
+  if (p->nu_field != nullptr)
+    return set_error(MFG_ERR_UNSUPPORTED, "mfg_apply_precond_noalloc: a viscosity field needs plan-built factors");
   const Geom g = make_geom(*p);
   if (g.n > kNaMaxN || g.nx > kNaMaxAxis || g.ny > kNaMaxAxis || g.nt > kNaMaxNt)
     return set_error(MFG_ERR_INVALID_ARG,

@@ -40,15 +40,16 @@ def test_struct_layout_matches_header(tmp_path):
     L = _lib()
     src = tmp_path / "layout.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mfg.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(mfg_problem), '
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mfg_problem), '
                    'sizeof(mfg_stats), offsetof(mfg_problem, precision), offsetof(mfg_problem, nu), '
-                   'offsetof(mfg_stats, cg_iters), offsetof(mfg_stats, sigma));return 0;}\n')
+                   'offsetof(mfg_stats, cg_iters), offsetof(mfg_stats, sigma), '
+                   'offsetof(mfg_problem, nu_field));return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert vals == [ctypes.sizeof(L.MfgProblem), ctypes.sizeof(L.MfgStats),
                     L.MfgProblem.precision.offset, L.MfgProblem.nu.offset,
-                    L.MfgStats.cg_iters.offset, L.MfgStats.sigma.offset]
+                    L.MfgStats.cg_iters.offset, L.MfgStats.sigma.offset, L.MfgProblem.nu_field.offset]
 
 
 def test_plan_rejects_invalid_problems_without_gpu():
@@ -64,6 +65,26 @@ def test_plan_rejects_invalid_problems_without_gpu():
             L.mfg_plan(bad)
         assert e.value.code == code
         assert L.mfg_last_error()
+
+
+def test_plan_rejects_invalid_viscosity_fields_without_gpu():
+    """A viscosity field is read and checked on the host: negative or non-finite
+    values are invalid, and the exact time solve (l = 0) does not take a field."""
+    import numpy as np
+    import mfg_inputs as mi
+    L = _lib()
+    base = mi.small(2, l=1)["problem"]
+    good = np.full(base["n"], 0.1)
+    neg, nan = good.copy(), good.copy()
+    neg[1, 2] = -1e-3
+    nan[0, 0] = np.nan
+    for bad, code, text in ((dict(base, nu_field=neg), L.MFG_ERR_INVALID_ARG, "viscosity"),
+                            (dict(base, nu_field=nan), L.MFG_ERR_INVALID_ARG, "viscosity"),
+                            (dict(base, nu_field=good, l=0), L.MFG_ERR_UNSUPPORTED, "l = 1 or 2")):
+        with pytest.raises(L.MfgError) as e:
+            L.mfg_plan(bad)
+        assert e.value.code == code
+        assert text in L.mfg_last_error()
 
 
 def test_precision_codes_match_header():
