@@ -354,6 +354,47 @@ def exact_time_measure(L, dev, stream):
     return out
 
 
+def varnu_measure(L, dev, stream, cp=100, reps=5):
+    """A viscosity field nu(x) (smooth, 10:1 around 1e-2, seed 7) on the 2-D
+    Neumann 128^2 x 64 grid, headline precision: plan build (host banded
+    Cholesky per time frequency, the LU option of Alg. 1), one P^-1 apply next
+    to the constant-nu apply of the same grid, and `cp` CP iterations per step."""
+    import time
+
+    import torch
+    try:
+        inst = mi.config_varnu(n=128, nt=64)
+        p = dict(inst["problem"], max_cp=cp, cg_tol=CG_TOL, precision=PRECISION)
+        t0 = time.perf_counter()
+        fx = Fixed(L, dev, [inst], [p], stream)
+        plan_s = time.perf_counter() - t0
+        out = fx.timed(steps=1, warmup=1)
+        n = fx.sizes["dual"]
+        r = torch.randn(n, dtype=torch.float64, device=dev)
+        z = torch.empty_like(r)
+        pc = {k: v for k, v in p.items() if k != "nu_field"}
+        const = L.mfg_plan(pc)
+
+        def timed(plan):
+            for _ in range(2):
+                L.mfg_apply_precond(plan, 0, r, z, stream=stream)
+            torch.cuda.synchronize()
+            a, b = _events(stream)
+            a.record(stream)
+            for _ in range(reps):
+                L.mfg_apply_precond(plan, 0, r, z, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            return 1e3 * a.elapsed_time(b) / reps
+
+        out.update(workload=f"2-D Neumann 128^2 x 64, nu(x) smooth 10:1 around 1e-2, {cp} CP iterations per step, "
+                            f"{PRECISION}", plan_build_s=plan_s, precond_apply_us=timed(fx.plan),
+                   constant_nu_precond_apply_us=timed(const))
+        return out
+    except Exception as e:  # an extra line only: never let it break the benchmark line
+        return {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+
+
 def cufft_compare(L, dev, reps=10):
     """cuFFT as a timed comparison only: torch.fft's 2-D real FFT forward and
     inverse over the 128 planes of the headline grid (FP32), next to one
@@ -573,6 +614,7 @@ def run_gpu(args):  # noqa: C901
         extras["config2_four_viscosities"] = config2_measure(L, dev, stream, args.precision)
         extras["batch_uneven"] = batch_measure(L, dev, stream, args.precision)
         extras["exact_time_solve"] = exact_time_measure(L, dev, stream)
+        extras["viscosity_field"] = varnu_measure(L, dev, stream)
         extras["adjoint"] = adjoint_measure(L, dev)
         extras["cufft_comparison"] = cufft_compare(L, dev)
         if rank == 0:

@@ -15,10 +15,11 @@
 //   time forward (scatter to band order) -> L y = b -> L^T x = y -> time
 //   inverse (gather from band order).
 // The substitutions are sequential along the band: one CTA per frequency
-// walks its S points with a circular window of w+2 partial sums in shared
-// memory; the factor rows, contiguous in memory in the order they are used,
-// stream through a ring of shared-memory stages filled by cp.async several
-// stages ahead, so the loads never wait on the dependency chain.
+// walks its S points in blocks of up to 32 (a warp-shuffle triangular solve,
+// then a block update of the next w partial sums, held in a circular window
+// in shared memory); the factor rows, contiguous in memory in the order they
+// are used, stream through a ring of shared-memory stages filled by cp.async
+// several blocks ahead, so the loads never wait on the dependency chain.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -127,6 +128,28 @@ int band_row_words(int w, size_t elt) {
   return (w + 1 + per16 - 1) / per16 * per16;
 }
 
+// Launch shape of the substitutions.  G: the block of steps, the largest power
+// of two <= 32 whose stage (G factor rows, plus the G x G inverse of the
+// block's triangle when G >= 4) fits in kBandStageBytes, at least 1.
+struct BandShape {
+  int wp, G, inv, stage, threads;
+  size_t smem;
+};
+
+template <typename T>
+BandShape band_shape(int w) {
+  BandShape b;
+  b.wp = band_row_words(w, sizeof(T));
+  auto stage = [&](int G) { return G * b.wp + (G >= 4 ? G * G : 0); };
+  b.G = 1;
+  while (b.G < 32 && (size_t)stage(b.G * 2) * sizeof(T) <= (size_t)kBandStageBytes) b.G *= 2;
+  b.inv = b.G >= 4;
+  b.stage = stage(b.G);
+  b.threads = std::min(512, std::max(32, (w + 31) / 32 * 32));
+  b.smem = sizeof(T) * ((size_t)kBandRing * b.stage + (size_t)kBandRing * b.G + 32 + (size_t)w + b.G);
+  return b;
+}
+
 template <typename T>
 int build_factors(const Geom& g, const std::vector<Row>& chat, const std::vector<Row>& lhat,
                   const std::vector<int>& ipos, const double* lamt, int w, PrecTables* t,
@@ -136,6 +159,12 @@ int build_factors(const Geom& g, const std::vector<Row>& chat, const std::vector
   const size_t per = (size_t)S * wp;
   std::vector<T> Lc(per * nt, T(0)), Lr(per * nt, T(0));
   std::vector<int> bad((size_t)nt, 0);
+  // inverses of the full blocks' step-space triangles, per direction:
+  // Dinv[(k nblk + blk) G^2 + b G + a] = (T_blk^{-1})[a][b]
+  const BandShape bs = band_shape<T>(w);
+  const int G = bs.G, nblk = bs.inv ? S / G : 0;
+  const size_t perD = (size_t)nblk * G * G;
+  std::vector<T> Dc(perD * nt, T(0)), Dr(perD * nt, T(0));
   auto work = [&](int k0, int k1) {
     std::vector<double> A((size_t)S * (w + 1));
     for (int k = k0; k < k1; ++k) {
@@ -155,6 +184,35 @@ int build_factors(const Geom& g, const std::vector<Row>& chat, const std::vector
       if (!band_cholesky(A, S, w)) {
         bad[(size_t)k] = 1;
         continue;
+      }
+      // Step-space triangle of block blk (steps t0 .. t0+G-1): Tm[a][b] couples
+      // step t0+b to step t0+a at distance a - b (0 beyond w), the diagonal
+      // holds L_jj.  Forward: step t is band row t and the coupling is
+      // L_{t0+a, t0+b}; backward: step t is band row S-1-t and the coupling is
+      // L_{S-1-t0-b, S-1-t0-a}.  Inverted by forward substitution in FP64.
+      std::vector<double> Tm((size_t)G * G), Ti((size_t)G * G);
+      for (int dir = 0; dir < 2 && nblk > 0; ++dir) {
+        T* D = (dir == 0 ? Dc.data() : Dr.data()) + perD * k;
+        for (int blk = 0; blk < nblk; ++blk) {
+          const int t0 = blk * G;
+          std::fill(Tm.begin(), Tm.end(), 0.0);
+          for (int a = 0; a < G; ++a)
+            for (int b = 0; b <= a; ++b) {
+              const int d = a - b;
+              if (d > w) continue;
+              const int col = dir == 0 ? t0 + b : S - 1 - t0 - a;  // column of L in band storage
+              Tm[(size_t)a * G + b] = A[(size_t)col * (w + 1) + d];
+            }
+          for (int c = 0; c < G; ++c)  // column c of the inverse
+            for (int a = 0; a < G; ++a) {
+              double v = (a == c) ? 1.0 : 0.0;
+              for (int b = c; b < a; ++b) v -= Tm[(size_t)a * G + b] * Ti[(size_t)b * G + c];
+              Ti[(size_t)a * G + c] = (a >= c) ? v / Tm[(size_t)a * G + a] : 0.0;
+            }
+          T* Db = D + (size_t)blk * G * G;
+          for (int a = 0; a < G; ++a)
+            for (int b = 0; b < G; ++b) Db[(size_t)b * G + a] = (T)Ti[(size_t)a * G + b];
+        }
       }
       T* lc = Lc.data() + per * k;
       T* lr = Lr.data() + per * k;
@@ -180,18 +238,22 @@ int build_factors(const Geom& g, const std::vector<Row>& chat, const std::vector
     }
   T* dc = upload_vec(Lc);
   T* dr = upload_vec(Lr);
-  if (!dc || !dr) {
-    if (dc) cudaFree(dc);
-    if (dr) cudaFree(dr);
-    *err = "cudaMalloc failed for the banded factors";
-    return MFG_ERR_CUDA;
-  }
+  T* ic = nblk > 0 ? upload_vec(Dc) : nullptr;
+  T* ir = nblk > 0 ? upload_vec(Dr) : nullptr;
   if constexpr (sizeof(T) == 8) {
     t->bandc64 = dc;
     t->bandr64 = dr;
+    t->bandic64 = ic;
+    t->bandir64 = ir;
   } else {
     t->bandc32 = dc;
     t->bandr32 = dr;
+    t->bandic32 = ic;
+    t->bandir32 = ir;
+  }
+  if (!dc || !dr || (nblk > 0 && (!ic || !ir))) {
+    *err = "cudaMalloc failed for the banded factors";
+    return MFG_ERR_CUDA;  // the caller frees what was uploaded
   }
   return MFG_OK;
 }
@@ -308,126 +370,203 @@ __global__ void __launch_bounds__(256) k_time_xf(const TI* __restrict__ in, TO* 
   }
 }
 
-// One banded substitution per frequency (blockIdx.x = k), in band order.
-//   forward (BWD = false): L y = b, walking j = 0..S-1 with the column layout
-//     (row j of F: 1/L_jj, then L_{j+1+e, j});
-//   backward (BWD = true): L^T x = y, walking j = S-1..0 with the row layout
-//     (row j of F: 1/L_jj, then L_{j, j-1-e}).
-// Step j: x_j = acc_j / L_jj, then acc_i -= F_j[1+e] x_j for the w entries
-// i = j +- (1+e) still ahead, and the entry w+1 ahead enters the window.  The
-// window keeps entry i at slot i mod (w+2), so a step never writes the slot
-// it reads or the slot it refills.  Factor rows arrive through a ring of
-// kBandRing stages of G rows each (cp.async, 16-byte chunks), with the
-// refill values of each stage (4- or 8-byte copies); cp.async.wait_group only
-// waits for copies already issued, so the pipeline cannot stall for good.
-template <typename T, bool BWD>
-__global__ void __launch_bounds__(1024) k_band_pass(const T* __restrict__ rhs, T* __restrict__ sol,
-                                                    const T* __restrict__ F, int S, int w, int wp, int G,
-                                                    const DevScalars* sc) {
+// One banded substitution per frequency (blockIdx.x = k).  Both directions are
+// the same lower-triangular banded solve in step order t = 0..S-1:
+//   forward (BWD = false, L y = b): step t is band index j = t, and row j of
+//     the column layout (1/L_jj, then L_{j+d, j}, d = 1..w) couples step t to
+//     step t + d;
+//   backward (BWD = true, L^T x = y): step t is j = S-1-t, and row j of the
+//     row layout (1/L_jj, then L_{j, j-d}) again couples step t to step t + d.
+// Steps go in blocks of G (a power of two <= 32): warp 0 solves the block's
+// G x G triangle, for G >= 4 as one product with the triangle's inverse
+// (formed on the host in FP64 and streamed with the rows; lane a sums G
+// terms, no dependency chain), else with shuffles (lane b holds entry t0+b and
+// its row of the triangle in registers), then every thread
+// subtracts the block's contribution from one of the next w entries (a G-term
+// dot product out of shared memory): two barriers per G steps.  The window
+// keeps entry t at slot t mod (w+G); during a block it holds entries
+// t0 .. t0+G+w-1, and the slots of the G entries the block finishes take
+// entries t0+G+w .. t0+2G+w-1, read from b (no earlier step reaches them:
+// their distance is above w).  Factor rows and refill values of a block
+// arrive through a ring of kBandRing shared-memory stages filled by cp.async
+// (16-byte chunks; 4- or 8-byte refill copies) kBandRing-1 blocks ahead;
+// cp.async.wait_group only waits for copies already issued, so the pipeline
+// cannot stall for good.  A last block shorter than G takes the same steps
+// with run-time bounds.
+template <typename T, bool BWD, int G>
+__global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T* __restrict__ sol,
+                                                    const T* __restrict__ F, const T* __restrict__ Dinv,
+                                                    int S, int w, int wp, const DevScalars* sc) {
+  constexpr bool INV = G >= 4;                    // full blocks carry their triangle's inverse
   if (sc != nullptr && sc->cg_done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* ring = reinterpret_cast<T*>(smraw);               // kBandRing x G x wp
-  T* refill = ring + (size_t)kBandRing * G * wp;       // kBandRing x G
-  T* win = refill + (size_t)kBandRing * G;             // w + 2
-  const int k = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
-  const int W2 = w + 2;
+  const int stage = G * wp + (INV ? G * G : 0);
+  T* ring = reinterpret_cast<T*>(smraw);          // kBandRing x (G x wp rows [+ G x G inverse])
+  T* refill = ring + (size_t)kBandRing * stage;   // kBandRing x G
+  T* xs = refill + (size_t)kBandRing * G;         // the block's solution (32)
+  T* win = xs + 32;                               // w + G
+  const int k = blockIdx.x, tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int W2 = w + G;
   const T* Fk = F + (size_t)k * S * wp;
   const T* bk = rhs + (size_t)k * S;
   T* xk = sol + (size_t)k * S;
-  const int nst = (S + G - 1) / G;
-  // rows [lo, lo + cnt) of stage st, and the band index of step t
-  auto stage_lo = [&](int st) {
-    if (!BWD) return st * G;
-    return max(0, S - (st + 1) * G);
-  };
-  auto stage_cnt = [&](int st) {
-    const int a = st * G, b = min(S, a + G);
-    return b - a;
-  };
+  const int nst = (S + G - 1) / G, nblk = S / G;
+  const T* Dk = INV ? Dinv + (size_t)k * nblk * G * G : nullptr;
+  auto band = [&](int t) { return BWD ? S - 1 - t : t; };
   auto issue = [&](int st) {
     if (st < nst) {
-      const int lo = stage_lo(st), cnt = stage_cnt(st);
-      T* dst = ring + (size_t)(st % kBandRing) * G * wp;
+      const int t0 = st * G, cnt = min(G, S - t0);
+      const int lo = BWD ? S - t0 - cnt : t0;  // lowest band row of the block
+      char* dst = reinterpret_cast<char*>(ring + (size_t)(st % kBandRing) * stage);
       const char* g0 = reinterpret_cast<const char*>(Fk + (size_t)lo * wp);
       const int chunks = (int)((size_t)cnt * wp * sizeof(T) / 16);
-      for (int c = tid; c < chunks; c += nth) cp_async16(reinterpret_cast<char*>(dst) + 16 * (size_t)c, g0 + 16 * (size_t)c);
+      for (int c = tid; c < chunks; c += nth) cp_async16(dst + 16 * (size_t)c, g0 + 16 * (size_t)c);
+      if (INV && cnt == G) {
+        char* di = dst + (size_t)G * wp * sizeof(T);
+        const char* gi = reinterpret_cast<const char*>(Dk + (size_t)st * G * G);
+        const int ci = (int)((size_t)G * G * sizeof(T) / 16);
+        for (int c = tid; c < ci; c += nth) cp_async16(di + 16 * (size_t)c, gi + 16 * (size_t)c);
+      }
       if (tid < cnt) {
-        const int t = st * G + tid;
-        const int j = BWD ? S - 1 - t : t;
-        const int r = BWD ? j - w - 1 : j + w + 1;
-        if (r >= 0 && r < S) cp_async_small<sizeof(T)>(refill + (st % kBandRing) * G + tid, bk + r);
+        const int r = t0 + w + G + tid;
+        if (r < S) cp_async_small<sizeof(T)>(refill + (st % kBandRing) * G + tid, bk + band(r));
       }
     }
     cp_async_commit();
   };
-  // initial window: the w+1 entries nearest the start
-  for (int e = tid; e <= w && e < S; e += nth) {
-    const int i = BWD ? S - 1 - e : e;
-    win[i % W2] = bk[i];
-  }
+  for (int e = tid; e < W2 && e < S; e += nth) win[e] = bk[band(e)];
   for (int st = 0; st < kBandRing - 1; ++st) issue(st);
-  int sj = BWD ? (S - 1) % W2 : 0;  // slot of the current entry j
   for (int st = 0; st < nst; ++st) {
     cp_async_wait<kBandRing - 2>();
     __syncthreads();
     issue(st + kBandRing - 1);
-    const T* rows = ring + (size_t)(st % kBandRing) * G * wp;
-    const T* rv = refill + (st % kBandRing) * G;
-    const int lo = stage_lo(st), cnt = stage_cnt(st);
-    for (int u = 0; u < cnt; ++u) {
-      const int t = st * G + u;
-      const int j = BWD ? S - 1 - t : t;
-      const T* f = rows + (size_t)(j - lo) * wp;
-      const T xj = win[sj] * f[0];
+    const int t0 = st * G, cnt = min(G, S - t0);
+    const int lo = BWD ? S - t0 - cnt : t0;
+    const T* rows = ring + (size_t)(st % kBandRing) * stage;
+    if (cnt == G) {
+      // factor row of step t0 + b inside the stage (compile-time index)
+#define ROW(b) (rows + (size_t)(BWD ? (G - 1 - (b)) : (b)) * wp)
+      if (INV) {
+        // x = T^{-1} acc with the block's precomputed inverse (transposed in
+        // the stage): G independent FMAs per lane, no dependency chain
+        if (warp == 0) {
+          const T* Di = rows + (size_t)G * wp;
+          const T accl = lane < G ? win[(t0 + lane) % W2] : T(0);
+          const int ml = lane < G ? lane : 0;
+          T x = T(0);
+#pragma unroll
+          for (int b = 0; b < G; ++b) x = fma(Di[b * G + ml], __shfl_sync(0xffffffffu, accl, b), x);
+          if (lane < G) xs[lane] = x;
+        }
+      } else if (warp == 0) {
+        T cf[G];
+#pragma unroll
+        for (int b = 0; b < G; ++b) {
+          const int d = lane - b;
+          const bool on = d > 0 && d <= w && lane < G;
+          const T v = ROW(b)[on ? d : 0];  // in-bounds address either way
+          cf[b] = on ? v : T(0);
+        }
+        const int ml = lane < G ? lane : 0;
+        const T inv = rows[(size_t)(BWD ? G - 1 - ml : ml) * wp];
+        T acc = lane < G ? win[(t0 + lane) % W2] : T(0);
+        T mine = T(0);
+#pragma unroll
+        for (int b = 0; b < G; ++b) {
+          const T xb = __shfl_sync(0xffffffffu, acc * inv, b);
+          if (lane == b) mine = xb;
+          acc = fma(-cf[b], xb, acc);
+        }
+        if (lane < G) xs[lane] = mine;
+      }
+      __syncthreads();
+      T xr[G];
+#pragma unroll
+      for (int b = 0; b < G; ++b) xr[b] = xs[b];
       for (int e = tid; e < w; e += nth) {
-        const int i = BWD ? j - 1 - e : j + 1 + e;
-        if (i >= 0 && i < S) {
-          int sl = BWD ? sj - 1 - e : sj + 1 + e;
-          sl += (sl < 0) ? W2 : ((sl >= W2) ? -W2 : 0);
-          win[sl] -= f[1 + e] * xj;
+        const int i = t0 + G + e;
+        if (i < S) {
+          T acc = T(0);
+#pragma unroll
+          for (int b = 0; b < G; ++b) {
+            const int d = G + e - b;
+            const T v = ROW(b)[d <= w ? d : 0];  // in-bounds address either way
+            if (d <= w) acc = fma(v, xr[b], acc);
+          }
+          win[i % W2] -= acc;
         }
       }
-      if (tid == 0) {
-        xk[j] = xj;
-        const int r = BWD ? j - w - 1 : j + w + 1;
-        if (r >= 0 && r < S) {
-          const int sl = BWD ? (sj + 1 == W2 ? 0 : sj + 1) : (sj == 0 ? W2 - 1 : sj - 1);
-          win[sl] = rv[u];
+#undef ROW
+    } else {
+      auto row = [&](int b) { return rows + (size_t)(band(t0 + b) - lo) * wp; };
+      if (warp == 0) {
+        T acc = lane < cnt ? win[(t0 + lane) % W2] : T(0);
+        for (int b = 0; b < cnt; ++b) {
+          const T* f = row(b);
+          const T xb = __shfl_sync(0xffffffffu, acc, b) * f[0];
+          const int d = lane - b;
+          if (d > 0 && d <= w && lane < cnt) acc = fma(-f[d], xb, acc);
+          if (lane == b) xs[b] = xb;
         }
       }
       __syncthreads();
-      sj = BWD ? (sj == 0 ? W2 - 1 : sj - 1) : (sj + 1 == W2 ? 0 : sj + 1);
+      for (int e = tid; e < w; e += nth) {
+        const int i = t0 + cnt + e;
+        if (i < S) {
+          T acc = T(0);
+          for (int b = 0; b < cnt; ++b) {
+            const int d = cnt + e - b;
+            if (d <= w) acc = fma(row(b)[d], xs[b], acc);  // d >= 1
+          }
+          win[i % W2] -= acc;
+        }
+      }
+    }
+    if (tid < cnt) {
+      const int r = t0 + w + G + tid;
+      if (r < S) win[r % W2] = refill[(st % kBandRing) * G + tid];
+      xk[band(t0 + tid)] = xs[tid];
     }
   }
   cp_async_wait<0>();
 }
 
-struct BandShape {
-  int wp, G, threads;
-  size_t smem;
-};
-
-template <typename T>
-BandShape band_shape(int w) {
-  BandShape b;
-  b.wp = band_row_words(w, sizeof(T));
-  b.G = std::max(1, std::min(16, kBandStageBytes / (int)(b.wp * sizeof(T))));
-  b.threads = std::min(1024, (w + 31) / 32 * 32);
-  b.smem = sizeof(T) * ((size_t)kBandRing * b.G * b.wp + (size_t)kBandRing * b.G + (size_t)w + 2);
-  return b;
+template <typename T, bool BWD>
+void launch_band_pass(const BandShape& b, int nt, const T* in, T* out, const T* F, const T* Dinv, int S,
+                      int w, const DevScalars* sc, cudaStream_t s) {
+  switch (b.G) {
+#define MFG_BAND_G(GG) \
+  case GG: k_band_pass<T, BWD, GG><<<nt, b.threads, b.smem, s>>>(in, out, F, Dinv, S, w, b.wp, sc); break;
+    MFG_BAND_G(32) MFG_BAND_G(16) MFG_BAND_G(8) MFG_BAND_G(4) MFG_BAND_G(2) MFG_BAND_G(1)
+#undef MFG_BAND_G
+    default: break;
+  }
 }
 
 template <typename T>
 void precond_band_typed(const Geom& g, const PrecTables& t, const T* V, const T* Lc, const T* Lr,
-                        const double* r, double* z, T* w0, T* w1, const DevScalars* sc, cudaStream_t s) {
+                        const T* Ic, const T* Ir, const double* r, double* z, T* w0, T* w1,
+                        const DevScalars* sc, cudaStream_t s) {
   const int S = g.S, nt = g.nt, w = t.band_w;
   const size_t tsm = sizeof(T) * (size_t)nt * 32;
   const int tb = (S + 31) / 32;
   k_time_xf<double, T, T, false, true><<<tb, 256, tsm, s>>>(r, w0, V, t.band_perm, nt, S, sc);
   const BandShape b = band_shape<T>(w);
-  k_band_pass<T, false><<<nt, b.threads, b.smem, s>>>(w0, w1, Lc, S, w, b.wp, b.G, sc);
-  k_band_pass<T, true><<<nt, b.threads, b.smem, s>>>(w1, w0, Lr, S, w, b.wp, b.G, sc);
+  launch_band_pass<T, false>(b, nt, w0, w1, Lc, Ic, S, w, sc, s);
+  launch_band_pass<T, true>(b, nt, w1, w0, Lr, Ir, S, w, sc, s);
   k_time_xf<T, double, T, true, false><<<tb, 256, tsm, s>>>(w0, z, V, t.band_perm, nt, S, sc);
+}
+
+template <typename T>
+int band_attrs(int smem) {
+  int bad = 0;
+#define MFG_BAND_ATTR(GG)                                                                                \
+  bad |= cudaFuncSetAttribute(k_band_pass<T, false, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != \
+         cudaSuccess;                                                                                    \
+  bad |= cudaFuncSetAttribute(k_band_pass<T, true, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess;
+  MFG_BAND_ATTR(32) MFG_BAND_ATTR(16) MFG_BAND_ATTR(8) MFG_BAND_ATTR(4) MFG_BAND_ATTR(2) MFG_BAND_ATTR(1)
+#undef MFG_BAND_ATTR
+  return bad;
 }
 
 }  // namespace
@@ -436,19 +575,13 @@ void precond_band_typed(const Geom& g, const PrecTables& t, const T* V, const T*
 // to kBandMaxW); called once per device before any launch or capture.
 int band_configure() {
   int bad = 0;
-  const size_t s64 = std::max(band_shape<double>(kBandMaxW).smem, band_shape<double>(8).smem);
-  const size_t s32 = std::max(band_shape<float>(kBandMaxW).smem, band_shape<float>(8).smem);
   size_t m64 = 0, m32 = 0;
-  for (int w = 1; w <= kBandMaxW; w = w < 64 ? w + 1 : w + 32) {
+  for (int w = 1; w <= kBandMaxW; ++w) {
     m64 = std::max(m64, band_shape<double>(w).smem);
     m32 = std::max(m32, band_shape<float>(w).smem);
   }
-  m64 = std::max(m64, s64);
-  m32 = std::max(m32, s32);
-  bad |= cudaFuncSetAttribute(k_band_pass<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m64) != cudaSuccess;
-  bad |= cudaFuncSetAttribute(k_band_pass<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m64) != cudaSuccess;
-  bad |= cudaFuncSetAttribute(k_band_pass<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m32) != cudaSuccess;
-  bad |= cudaFuncSetAttribute(k_band_pass<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m32) != cudaSuccess;
+  bad |= band_attrs<double>((int)m64);
+  bad |= band_attrs<float>((int)m32);
   const int t64 = (int)(sizeof(double) * kMaxNt * 32), t32 = (int)(sizeof(float) * kMaxNt * 32);
   bad |= cudaFuncSetAttribute(k_time_xf<double, double, double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, t64) != cudaSuccess;
   bad |= cudaFuncSetAttribute(k_time_xf<double, double, double, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, t64) != cudaSuccess;
@@ -460,9 +593,11 @@ int band_configure() {
 void launch_precond_band(const Geom& g, const PrecTables& t, int precision, const double* r, double* z,
                          double* work64, float* work32, const DevScalars* sc, cudaStream_t s) {
   if (precision == MFG_FP64)
-    precond_band_typed<double>(g, t, t.Vt64, t.bandc64, t.bandr64, r, z, work64, work64 + g.n, sc, s);
+    precond_band_typed<double>(g, t, t.Vt64, t.bandc64, t.bandr64, t.bandic64, t.bandir64, r, z, work64,
+                               work64 + g.n, sc, s);
   else
-    precond_band_typed<float>(g, t, t.Vt32, t.bandc32, t.bandr32, r, z, work32, work32 + g.n, sc, s);
+    precond_band_typed<float>(g, t, t.Vt32, t.bandc32, t.bandr32, t.bandic32, t.bandir32, r, z, work32,
+                              work32 + g.n, sc, s);
 }
 
 }  // namespace mfg

@@ -141,6 +141,10 @@ struct PrecTables {
   // otherwise.
   double *bandc64 = nullptr, *bandr64 = nullptr;
   float *bandc32 = nullptr, *bandr32 = nullptr;
+  // Inverses of the G x G step-space triangles of the full blocks of the
+  // substitutions (forward: c, backward: r; null when G < 4), transposed.
+  double *bandic64 = nullptr, *bandir64 = nullptr;
+  float *bandic32 = nullptr, *bandir32 = nullptr;
 };
 // Tensor-core time pass (MFG_MIXED_TC), for N_t in {32, 64, 128}.
 bool time_tc_supported(int nt);
