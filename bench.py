@@ -677,11 +677,17 @@ def run_kernels_only(args):
     """Three launches each of the standalone AAt, preconditioner and prox-step
     entry points (a short program for ncu captures).  --small takes the
     512^2 x 32 Neumann grid (vectors of 67 MB, still larger than L2 with the
-    stencil intermediates) instead of the headline's 512^2 x 128."""
+    stencil intermediates) instead of the headline's 512^2 x 128.  --field
+    takes the viscosity-field workload instead (128^2 x 64 Neumann, 10:1
+    smooth field; --small: 64^2 x 32), whose preconditioner runs the banded
+    per-frequency solves."""
     import torch
     import paper_2507_01958_gb300 as pkg
     L = pkg.lib()
-    inst = mi.config3(nt=32) if args.small else mi.config3()
+    if args.field:
+        inst = mi.config_varnu(n=64, nt=32) if args.small else mi.config_varnu()
+    else:
+        inst = mi.config3(nt=32) if args.small else mi.config3()
     p = dict(inst["problem"], max_cp=1, cg_tol=CG_TOL, precision=args.precision)
     plan = L.mfg_plan(p)
     n = p["nt"] * p["n"][0] * p["n"][1]
@@ -752,6 +758,8 @@ def main(argv=None):
     ap.add_argument("--kernels-only", action="store_true",
                     help="three launches of each standalone hot kernel (for ncu captures)")
     ap.add_argument("--small", action="store_true", help="--kernels-only on the 512^2 x 32 Neumann grid")
+    ap.add_argument("--field", action="store_true",
+                    help="--kernels-only on the viscosity-field workload (banded preconditioner)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch choices instead of the autotuner's measured ones")
     ap.add_argument("--eager", action="store_true",

@@ -393,6 +393,28 @@ __global__ void __launch_bounds__(256) k_time_xf(const TI* __restrict__ in, TO* 
 // cp.async.wait_group only waits for copies already issued, so the pipeline
 // cannot stall for good.  A last block shorter than G takes the same steps
 // with run-time bounds.
+// xr[0..G) = xs[0..G) with 16-byte shared loads (xs is 16-byte aligned)
+template <typename T, int G>
+__device__ __forceinline__ void load_block(const T* xs, T (&xr)[G]) {
+  constexpr int V = 16 / (int)sizeof(T);
+  if constexpr (G % V == 0 && sizeof(T) == 4) {
+#pragma unroll
+    for (int b = 0; b < G; b += 4) {
+      const float4 q = *reinterpret_cast<const float4*>(xs + b);
+      xr[b] = q.x; xr[b + 1] = q.y; xr[b + 2] = q.z; xr[b + 3] = q.w;
+    }
+  } else if constexpr (G % V == 0 && sizeof(T) == 8) {
+#pragma unroll
+    for (int b = 0; b < G; b += 2) {
+      const double2 q = *reinterpret_cast<const double2*>(xs + b);
+      xr[b] = q.x; xr[b + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < G; ++b) xr[b] = xs[b];
+  }
+}
+
 template <typename T, bool BWD, int G>
 __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T* __restrict__ sol,
                                                     const T* __restrict__ F, const T* __restrict__ Dinv,
@@ -436,6 +458,9 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
   };
   for (int e = tid; e < W2 && e < S; e += nth) win[e] = bk[band(e)];
   for (int st = 0; st < kBandRing - 1; ++st) issue(st);
+  // slot of entry t0 + x is s0 + x, less W2 past the end (x < W2): no divisions
+  int s0 = 0;
+  auto slot = [&](int x) { const int q = s0 + x; return q >= W2 ? q - W2 : q; };
   for (int st = 0; st < nst; ++st) {
     cp_async_wait<kBandRing - 2>();
     __syncthreads();
@@ -451,12 +476,12 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
         // the stage): G independent FMAs per lane, no dependency chain
         if (warp == 0) {
           const T* Di = rows + (size_t)G * wp;
-          const T accl = lane < G ? win[(t0 + lane) % W2] : T(0);
+          const T accl = lane < G ? win[slot(lane)] : T(0);
           const int ml = lane < G ? lane : 0;
-          T x = T(0);
+          T xa[4] = {T(0), T(0), T(0), T(0)};  // four independent FMA chains
 #pragma unroll
-          for (int b = 0; b < G; ++b) x = fma(Di[b * G + ml], __shfl_sync(0xffffffffu, accl, b), x);
-          if (lane < G) xs[lane] = x;
+          for (int b = 0; b < G; ++b) xa[b & 3] = fma(Di[b * G + ml], __shfl_sync(0xffffffffu, accl, b), xa[b & 3]);
+          if (lane < G) xs[lane] = (xa[0] + xa[1]) + (xa[2] + xa[3]);
         }
       } else if (warp == 0) {
         T cf[G];
@@ -469,7 +494,7 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
         }
         const int ml = lane < G ? lane : 0;
         const T inv = rows[(size_t)(BWD ? G - 1 - ml : ml) * wp];
-        T acc = lane < G ? win[(t0 + lane) % W2] : T(0);
+        T acc = lane < G ? win[slot(lane)] : T(0);
         T mine = T(0);
 #pragma unroll
         for (int b = 0; b < G; ++b) {
@@ -481,26 +506,30 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
       }
       __syncthreads();
       T xr[G];
-#pragma unroll
-      for (int b = 0; b < G; ++b) xr[b] = xs[b];
+      load_block<T, G>(xs, xr);
       for (int e = tid; e < w; e += nth) {
         const int i = t0 + G + e;
         if (i < S) {
-          T acc = T(0);
+          T acc[4] = {T(0), T(0), T(0), T(0)};  // four independent FMA chains
+          if (G + e <= w) {  // every row of the block reaches entry i
 #pragma unroll
-          for (int b = 0; b < G; ++b) {
-            const int d = G + e - b;
-            const T v = ROW(b)[d <= w ? d : 0];  // in-bounds address either way
-            if (d <= w) acc = fma(v, xr[b], acc);
+            for (int b = 0; b < G; ++b) acc[b & 3] = fma(ROW(b)[G + e - b], xr[b], acc[b & 3]);
+          } else {
+#pragma unroll
+            for (int b = 0; b < G; ++b) {
+              const int d = G + e - b;
+              const T v = ROW(b)[d <= w ? d : 0];  // in-bounds address either way
+              if (d <= w) acc[b & 3] = fma(v, xr[b], acc[b & 3]);
+            }
           }
-          win[i % W2] -= acc;
+          win[slot(G + e)] -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
         }
       }
 #undef ROW
     } else {
       auto row = [&](int b) { return rows + (size_t)(band(t0 + b) - lo) * wp; };
       if (warp == 0) {
-        T acc = lane < cnt ? win[(t0 + lane) % W2] : T(0);
+        T acc = lane < cnt ? win[slot(lane)] : T(0);
         for (int b = 0; b < cnt; ++b) {
           const T* f = row(b);
           const T xb = __shfl_sync(0xffffffffu, acc, b) * f[0];
@@ -518,15 +547,16 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
             const int d = cnt + e - b;
             if (d <= w) acc = fma(row(b)[d], xs[b], acc);  // d >= 1
           }
-          win[i % W2] -= acc;
+          win[slot(cnt + e)] -= acc;
         }
       }
     }
     if (tid < cnt) {
       const int r = t0 + w + G + tid;
-      if (r < S) win[r % W2] = refill[(st % kBandRing) * G + tid];
+      if (r < S) win[slot(tid)] = refill[(st % kBandRing) * G + tid];  // r = t0 + tid (mod W2)
       xk[band(t0 + tid)] = xs[tid];
     }
+    s0 = slot(G);
   }
   cp_async_wait<0>();
 }
