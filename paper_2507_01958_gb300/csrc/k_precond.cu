@@ -671,6 +671,7 @@ int precond_configure() {
 #undef MFG_TF_ATTR
   bad |= fft_configure() != MFG_OK;
   bad |= band_configure() != MFG_OK;
+  bad |= prox_configure() != MFG_OK;
   bad |= time_tc_configure() != MFG_OK;
   return bad ? MFG_ERR_CUDA : MFG_OK;
 }

@@ -15,6 +15,8 @@
 // Root finder: Newton from m = 0 with the bracket [lo, hi] kept by the sign of
 // h and a bisection step whenever Newton leaves it (for f_b = 0, h is concave
 // and Newton from the left never does); see prox_cell for the precision split.
+#include <algorithm>
+
 #include "df64.cuh"
 #include "mfg_internal.cuh"
 #include "reduce.cuh"
@@ -388,11 +390,35 @@ __global__ void __launch_bounds__(kThreads) k_prox_plain(Geom g, Coef cf, double
   }
 }
 
+// One wave of resident blocks per instantiation (SMs x blocks per SM from the
+// occupancy calculator), set by prox_configure: the prox step is FP64-bound
+// with ~100 registers a thread, so a grid past one wave only adds a tail.
+int g_prox_wave[8] = {kRedBlocks, kRedBlocks, kRedBlocks, kRedBlocks, kRedBlocks, kRedBlocks, kRedBlocks,
+                      kRedBlocks};
+
+int prox_configure() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MFG_ERR_CUDA;
+  const void* fns[8] = {(const void*)k_prox_cp<0, false, false>, (const void*)k_prox_cp<0, false, true>,
+                        (const void*)k_prox_cp<0, true, false>,  (const void*)k_prox_cp<0, true, true>,
+                        (const void*)k_prox_cp<1, false, false>, (const void*)k_prox_cp<1, false, true>,
+                        (const void*)k_prox_cp<1, true, false>,  (const void*)k_prox_cp<1, true, true>};
+  for (int i = 0; i < 8; ++i) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fns[i], kThreads, 0) != cudaSuccess) return MFG_ERR_CUDA;
+    g_prox_wave[i] = std::max(1, std::min(kVecBlocksMax, sms * std::max(occ, 1)));
+  }
+  return MFG_OK;
+}
+
 void launch_prox_cp(const Geom& g, const Coef& cf, const double* z, double* y, double* ybar,
                     const double* V, const double* W, double* partials, DevScalars* sc,
                     cudaGraphConditionalHandle h, int use_handle, cudaStream_t s, double* Az,
                     const double* rfin) {
-  const int nb = red_blocks(g.n, g.vec_blocks);
+  const int idx = (g.actx ? 4 : 0) + (cf.qprime != 2.0 ? 2 : 0) + (g.kfy != nullptr ? 1 : 0);
+  const int nb = red_blocks(g.n, g_prox_wave[idx]);
   // the general-q' root finder and the viscosity field are their own
   // instantiations, so the q' = 2, constant-nu kernel keeps its registers
 #define MFG_PROX_CP(A, Q, N) \

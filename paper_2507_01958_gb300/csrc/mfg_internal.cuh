@@ -224,5 +224,6 @@ void launch_prox_cp(const Geom& g, const Coef& cf, const double* z, double* y, d
                     double* Az = nullptr, const double* rfin = nullptr);
 void launch_prox_plain(const Geom& g, const Coef& cf, double tau, const double* v, double* y,
                        const double* V, const double* W, cudaStream_t s);
+int prox_configure();
 
 }  // namespace mfg

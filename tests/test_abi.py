@@ -102,3 +102,17 @@ def test_precision_codes_match_header():
     with pytest.raises(L.MfgError) as e:
         L.mfg_plan(dict(base), precision=7)
     assert e.value.code == L.MFG_ERR_INVALID_ARG
+
+
+def test_noalloc_rejects_viscosity_field_without_gpu():
+    """The allocation-free apply has no banded factors: a viscosity field is
+    refused on the host, before any device call (the pointers are never read)."""
+    import ctypes
+    import numpy as np
+    import mfg_inputs as mi
+    L = _lib()
+    base = mi.small(3, l=1)["problem"]
+    p = L.problem_struct(dict(base, nu_field=np.full(base["n"], 0.2)), "mixed")
+    rc = L.LIB.mfg_apply_precond_noalloc(ctypes.byref(p), ctypes.c_void_p(256), ctypes.c_void_p(512), None)
+    assert rc == L.MFG_ERR_UNSUPPORTED
+    assert "viscosity field" in L.mfg_last_error()

@@ -11,7 +11,10 @@ per-frequency systems of Alg. 1, Sec. 4.1).
     dimensions, with smooth and discontinuous fields;
   - a constant field against the constant-nu path (FFT preconditioner);
   - a 64^2 x 32 Neumann grid with a 10:1 smooth field against the oracle's
-    inexact solve, counting PCG iterations."""
+    inexact solve, counting PCG iterations;
+  - a field instance batched with a constant-nu one (bitwise equal to the solo
+    solves), both stop references and the adaptive PCG rule, general q';
+  - the adjoint refuses a field (MFG_ERR_UNSUPPORTED)."""
 import numpy as np
 import pytest
 
@@ -188,3 +191,84 @@ def test_field_neumann_64_against_oracle():
     print(f"\nfield 64^2 x 32 Neumann: rel err {err:.1e}; {dev_cg:.2f} PCG per CP (oracle at 1e-12: {ora_cg:.2f})")
     assert err <= 1e-8
     assert dev_cg <= ora_cg + 1.0
+
+
+def _batch_solve(insts, iters, precision):
+    import torch
+    L = lib()
+    probs = [dict(i["problem"], max_cp=iters, cg_tol=1e-12, precision=precision) for i in insts]
+    plan = L.mfg_plan(probs)
+    cat = lambda k: dev(np.concatenate([np.asarray(i[k]).reshape(-1) for i in insts]))
+    y = cat("y0")
+    ybar = y.clone()
+    z = torch.zeros(L.mfg_sizes(plan)["dual"], dtype=torch.float64, device="cuda")
+    rc, st = L.mfg_solve(plan, cat("m0"), cat("V"), cat("W"), y, ybar, z)
+    assert rc == 0
+    outs = []
+    for b in range(len(insts)):
+        lay = L.mfg_layout(plan, b)
+        cn = lay["c"] * lay["n"]
+        outs.append((host(y)[lay["primal_off"]:lay["primal_off"] + cn], st[b]))
+    return outs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_tc"])
+def test_field_in_uneven_batch(precision):
+    """A field instance and a constant-nu instance in one plan (one CUDA graph):
+    each equals its own solo solve bit for bit and the oracle at the CP bound."""
+    a = _inst(CASES[0])
+    b = mi.small(41, nx=9, ny=14, nt=6, bc=("periodic", "neumann"))
+    iters = 10
+    batched = _batch_solve([a, b], iters, precision)
+    for inst, (yb, st) in zip([a, b], batched):
+        assert st.status == 0 and st.cp_iters == iters
+        ys, _ = _batch_solve([inst], iters, precision)[0]
+        assert np.array_equal(yb, ys)
+    ref = Solver(a["problem"], a["m0"], a["V"], a["W"], method="lu").run(a["y0"], iters=iters)
+    assert rel(batched[0][0], ref["y"]) <= max(1e-8, 10.0 * _field_cond(a["problem"]) * 2.0 ** -53)
+
+
+@pytest.mark.parametrize("cg_ref,cg_rule", [("resid", 0), ("rhs", 1), ("resid", 1)])
+def test_field_stop_rules_match_oracle(cg_ref, cg_rule):
+    """Both stop references and the paper's adaptive rule with a field, FP64:
+    the device's PCG counts equal the oracle's (the same P up to rounding)."""
+    import torch
+    inst = _inst(CASES[2])
+    p = dict(inst["problem"], max_cp=8, cg_tol=1e-10, cg_ref=cg_ref, cg_rule=cg_rule)
+    L = lib()
+    plan = L.mfg_plan(p, precision="fp64")
+    y = dev(inst["y0"])
+    ybar = y.clone()
+    z = torch.zeros(ops.sizes(p)[1], dtype=torch.float64, device="cuda")
+    rc, st = L.mfg_solve(plan, dev(inst["m0"]), dev(inst["V"]), dev(inst["W"]), y, ybar, z)
+    assert rc == 0 and st[0].status == 0
+    ref = Solver(p, inst["m0"], inst["V"], inst["W"], method="pcg", cg_ref=cg_ref).run(inst["y0"], iters=8)
+    assert abs(st[0].cg_iters - sum(ref["cg"])) <= 2
+    assert rel(host(y), ref["y"]) <= 1e-6
+
+
+def test_field_general_hamiltonian():
+    """q' = 1.5 with a field: the general-q' prox and K_nu in the same kernel
+    instantiation, against the oracle's exact solves."""
+    inst = _inst(CASES[3])
+    inst["problem"]["qprime"] = 1.5
+    iters = 10
+    rc, st, y, _, _ = _run(inst, iters, "mixed_tc")
+    assert rc == 0 and st.status == 0
+    ref = Solver(inst["problem"], inst["m0"], inst["V"], inst["W"], method="lu").run(inst["y0"], iters=iters)
+    assert rel(y, ref["y"]) <= max(1e-8, 10.0 * _field_cond(inst["problem"]) * 2.0 ** -53)
+
+
+def test_field_adjoint_is_unsupported():
+    import torch
+    inst = _inst(CASES[0])
+    L = lib()
+    plan = L.mfg_plan(dict(inst["problem"], max_cp=2))
+    s, n, c = ops.sizes(inst["problem"])
+    y = dev(inst["y0"])
+    z = torch.zeros(n, dtype=torch.float64, device="cuda")
+    out = torch.zeros(s, dtype=torch.float64, device="cuda")
+    dnu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.MfgError) as e:
+        L.mfg_adjoint(plan, 0, y, z, torch.zeros_like(y), out, out.clone(), out.clone(), dnu)
+    assert e.value.code == L.MFG_ERR_UNSUPPORTED
