@@ -121,12 +121,37 @@ def loss_mT(prob, y, m_target):
     return float((diff * diff).sum() * vol), g
 
 
+def _nu_field_gradient(prob, mu_m, z, eta3, m):
+    """dloss/dnu(x) at every node for a viscosity field.  nu enters only through
+    K_nu = sum_axes D^1 diag(nu_face) (D^1)^T / dx^2 with nu_face the mean of the
+    face's two nodes, so dK_nu/dnu_a = sum over the faces f of node a of
+    (1/2) g_f g_f^T / dx^2 with g_f = (D^1)^T row f (the face difference), and
+      dloss/dnu_a = -(1/2) sum_k sum_{f of a} [(g_f.mu_m^k)(g_f.z^k) + (g_f.eta^k)(g_f.m^k)] / dx^2,
+    the same contraction as the scalar dnu with K split face by face."""
+    nt = prob["nt"]
+    nx, ny = prob["n"]
+    dx = ops.spacing(prob)
+    out = np.zeros((nx, ny))
+    for ax in range(prob["dim"]):
+        n_ax = (nx, ny)[ax]
+        d1, _ = ops.div_blocks(n_ax, prob["bc"][ax])
+        D = sp.kron(d1, sp.identity(ny)) if (prob["dim"] == 2 and ax == 0) else (
+            sp.kron(sp.identity(nx), d1) if prob["dim"] == 2 else d1)
+        cf = np.zeros(D.shape[1])
+        for k in range(nt):
+            g = lambda u: D.T @ np.asarray(u[k]).reshape(-1)
+            cf += g(mu_m) * g(z) + g(eta3) * g(m)
+        cf /= dx[ax] ** 2
+        # face f joins node f and its plus neighbour; each takes half
+        absD = abs(D).tocsr()
+        out += (-0.5 * (absD @ cf)).reshape(nx, ny)
+    return out
+
+
 def adjoint_gradients(prob, y, z, gy):
     """Solve K [mu; eta] = [g_A; 0] and contract: returns dict of dm0 (Nx, Ny),
-    dV (Nx, Ny), dW (Nx, Ny), dnu (float), plus mu, eta.  Constant viscosity
-    only (dnu is the derivative in the scalar nu)."""
-    if ops.has_nu_field(prob):
-        raise ValueError("adjoint_gradients: constant viscosity only")
+    dV (Nx, Ny), dW (Nx, Ny), dnu (float; with a viscosity field the (Nx, Ny)
+    derivative in the node values nu(x)), plus mu, eta."""
     C = ops.constraint(prob)
     act = active_mask(y)
     a = act.reshape(-1)
@@ -144,14 +169,19 @@ def adjoint_gradients(prob, y, z, gy):
     nx, ny = prob["n"]
     h = ops.dt(prob)
     eta3 = eta.reshape(nt, nx, ny)
-    _, Ksp = ops.spatial(prob)
-    Kz = np.stack([(Ksp @ np.asarray(z).reshape(nt, -1)[k]) for k in range(nt)]).reshape(nt, nx, ny)
-    Km = np.stack([(Ksp @ np.asarray(y)[0].reshape(nt, -1)[k]) for k in range(nt)]).reshape(nt, nx, ny)
+    if ops.has_nu_field(prob):
+        z3 = np.asarray(z).reshape(nt, nx, ny)
+        dnu = _nu_field_gradient(prob, mu[0], z3, eta3, np.asarray(y)[0].reshape(nt, nx, ny))
+    else:
+        _, Ksp = ops.spatial(prob)
+        Kz = np.stack([(Ksp @ np.asarray(z).reshape(nt, -1)[k]) for k in range(nt)]).reshape(nt, nx, ny)
+        Km = np.stack([(Ksp @ np.asarray(y)[0].reshape(nt, -1)[k]) for k in range(nt)]).reshape(nt, nx, ny)
+        dnu = float(-(mu[0] * Kz).sum() - (eta3 * Km).sum())
     return {
         "dm0": eta3[0] / h,
         "dV": -mu[0].sum(axis=0),
         "dW": -mu[0][-1] / h,
-        "dnu": float(-(mu[0] * Kz).sum() - (eta3 * Km).sum()),
+        "dnu": dnu,
         "mu": mu,
         "eta": eta3,
     }

@@ -186,3 +186,58 @@ def test_field_pcg_solver_matches_lu():
     b = Solver(p, inst["m0"], inst["V"], inst["W"], method="pcg").run(inst["y0"])
     assert np.linalg.norm(a["y"] - b["y"]) <= 1e-9 * np.linalg.norm(a["y"])
     assert max(b["cg"]) <= 30
+
+
+def _converged_field(seed, bc, kind="smooth"):
+    from oracle import adjoint as adj
+    inst = mi.small(seed, nx=5, ny=4, nt=4, bc=bc, nu=0.2, eps=0.0)
+    p = dict(inst["problem"], gamma=0.05)
+    p["nu_field"] = mi.viscosity_field(p, 0.2, 4.0, seed + 3, kind)
+    rng = np.random.default_rng(seed)
+    nx, ny = p["n"]
+    m0 = mi._normalise(1.0 + 0.3 * rng.uniform(size=(nx, ny)), p)
+    V = 0.3 * rng.normal(size=(nx, ny))
+    W = 0.2 * rng.normal(size=(nx, ny))
+    res = Solver(p, m0, V, W).run(mi.initial_iterate(p, m0), iters=1500)
+    y, z = adj.kkt_newton(p, res["y"], res["z"], m0, V, W)
+    mt = mi._normalise(1.0 + 0.3 * rng.uniform(size=(nx, ny)), p)
+    return p, m0, V, W, y, z, mt
+
+
+@pytest.mark.parametrize("bc", [("periodic", "periodic"), ("neumann", "periodic")])
+def test_field_adjoint_gradient_matches_finite_differences(bc):
+    """dloss/dnu(x) at sample nodes (and dloss/dm0, dV along a random direction)
+    against central differences through Newton-refined KKT solutions."""
+    from oracle import adjoint as adj
+    p, m0, V, W, y, z, mt = _converged_field(8, bc)
+    _, g = adj.loss_mT(p, y, mt)
+    gr = adj.adjoint_gradients(p, y, z, g)
+    assert gr["dnu"].shape == tuple(p["n"])
+    h = 1e-6
+
+    def loss(q, m0_=m0, V_=V):
+        y2, _ = adj.kkt_newton(q, y, z, m0_, V_, W, iters=12)
+        return adj.loss_mT(q, y2, mt)[0]
+
+    nu = np.asarray(p["nu_field"])
+    for (i, j) in ((0, 0), (2, 1), (4, 3)):
+        up, dn = nu.copy(), nu.copy()
+        up[i, j] += h
+        dn[i, j] -= h
+        fd = (loss(dict(p, nu_field=up)) - loss(dict(p, nu_field=dn))) / (2 * h)
+        assert abs(fd - gr["dnu"][i, j]) <= 1e-5 * max(1e-3, abs(fd)), ((i, j), fd, gr["dnu"][i, j])
+    d = np.random.default_rng(9).normal(size=m0.shape)
+    fd = (loss(p, m0_=m0 + h * d) - loss(p, m0_=m0 - h * d)) / (2 * h)
+    assert abs(fd - float((gr["dm0"] * d).sum())) <= 1e-5 * max(1e-3, abs(fd))
+
+
+def test_constant_field_gradient_sums_to_scalar():
+    """For a constant field the node derivatives add up to the scalar dnu
+    (each face's term is split half and half between its two nodes)."""
+    from oracle import adjoint as adj
+    from test_oracle_adjoint import _converged
+    p, m0, V, W, y, z, mt = _converged(5, ("neumann", "periodic"))
+    _, g = adj.loss_mT(p, y, mt)
+    scalar = adj.adjoint_gradients(p, y, z, g)["dnu"]
+    field = adj.adjoint_gradients(dict(p, nu_field=np.full(p["n"], p["nu"])), y, z, g)["dnu"]
+    assert abs(field.sum() - scalar) <= 1e-10 * max(1.0, abs(scalar))
