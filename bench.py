@@ -549,26 +549,29 @@ def run_gpu(args):  # noqa: C901
 
     # End to end through the host-buffer entry point: every step copies the
     # inputs and the start iterate from pinned host memory and reads the
-    # iterate back (copies inside the timed region).
+    # iterate back (copies inside the timed region).  Each timed step gets its
+    # own pinned start iterate, filled before the timed region (the call
+    # overwrites y, ybar, z with the result).
     pin = lambda a: torch.as_tensor(a).pin_memory()
     hm0, hV, hW = pin(main.host["m0"]), pin(main.host["V"]), pin(main.host["W"])
-    y0_h = torch.from_numpy(main.host["y0"])
-    hy, hyb = pin(main.host["y0"].copy()), pin(main.host["y0"].copy())
-    hz = torch.zeros(main.sizes["dual"], dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 2))
 
-    def host_step():
-        hy.copy_(y0_h)
-        hyb.copy_(y0_h)
-        hz.zero_()
+    def start_iterate():
+        return (pin(main.host["y0"].copy()), pin(main.host["y0"].copy()),
+                torch.zeros(main.sizes["dual"], dtype=torch.float64).pin_memory())
+
+    def host_step(bufs):
+        hy, hyb, hz = bufs
         return L.mfg_solve_host(main.plan, hm0, hV, hW, hy, hyb, hz, stream=stream)[1]
 
-    host_step()  # first call allocates the plan's staging buffers
-    e2e_steps = max(1, min(args.steps, 2))
+    host_step(start_iterate())  # first call allocates the plan's staging buffers
+    sets = [start_iterate() for _ in range(e2e_steps)]
     torch.cuda.synchronize()
     h0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        st = host_step()
+    for i in range(e2e_steps):
+        st = host_step(sets[i])
     h1 = time.perf_counter()
+    del sets
     t_e2e = reduce_max(h1 - h0, world, dev)
     cp_e2e = reduce_sum(float(sum(s.cp_iters for s in st) * e2e_steps), world, dev)
     sz = main.sizes

@@ -130,10 +130,11 @@ typedef struct {
  * 2 N_t Nx Ny (w+1) words, w the half-bandwidth (2 Ny on a Neumann x axis,
  * ~4 Ny + Ny on a periodic one), and O(N_t Nx Ny w^2) host work in mfg_plan.
  * Restrictions: l must be 1 or 2 (MFG_ERR_UNSUPPORTED for l = 0); w <= 4096
- * and factor storage <= 64 GiB (MFG_ERR_UNSUPPORTED beyond); mfg_adjoint and
- * mfg_apply_precond_noalloc return MFG_ERR_UNSUPPORTED; MFG_MIXED_DF runs its
- * AAt stencil in FP64 (as MFG_MIXED); the time transforms run on the CUDA cores
- * in every precision.  nu is ignored. */
+ * and factor storage <= 64 GiB (MFG_ERR_UNSUPPORTED beyond);
+ * mfg_apply_precond_noalloc returns MFG_ERR_UNSUPPORTED; mfg_adjoint returns
+ * the gradient with respect to nu(x) node by node; MFG_MIXED_DF runs its AAt
+ * stencil in FP64 (as MFG_MIXED); the time transforms run on the CUDA cores in
+ * every precision.  nu is ignored. */
 
 /* Per-instance run record.  On entry to mfg_solve, `ell`, `tau`, `sigma` are
  * the resume state (ell = 0 starts from tau0, sigma0); on return all fields
@@ -241,10 +242,13 @@ int mfg_apply_Ct(mfg_plan_t plan, int b, const double* p, double* x, void* strea
  *            the active set is read off y (m > 0, w components != 0)
  *   gy     : dloss/dy, c*n device doubles (same layout as y)
  *   dm0    : out, dloss/dm0, Nx*Ny           dV : out, dloss/dV(x), Nx*Ny
- *   dW     : out, dloss/dW(x), Nx*Ny or NULL dnu: out, dloss/dnu, 1 device double
+ *   dW     : out, dloss/dW(x), Nx*Ny or NULL dnu: out, dloss/dnu, 1 device double;
+ *            with a viscosity field, Nx*Ny device doubles: dloss/dnu(x) at the
+ *            nodes (nu_face = mean of its two nodes, so each face's term is
+ *            split half and half between them)
  *   tol, max_iter: relative tolerance and cap of the adjoint PCG
  *   st     : out; cg_iters = adjoint PCG iterations, r_last = final relative residual
- * Built for q' = 2 and a constant viscosity (MFG_ERR_UNSUPPORTED otherwise).
+ * Built for q' = 2 (MFG_ERR_UNSUPPORTED otherwise).
  * The adjoint system is solved through its Schur complement
  * C_A H^{-1} C_A^T with the plan's preconditioner P (eq. prec) inside PCG,
  * H being the per-cell Hessian of phi.  The first call allocates a c*n + n

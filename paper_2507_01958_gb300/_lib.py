@@ -152,10 +152,11 @@ def problem_struct(d, precision=None):
 class Plan:
     """Owns an mfg_plan_t; freed with mfg_destroy."""
 
-    def __init__(self, handle, batch, nts=()):
+    def __init__(self, handle, batch, nts=(), fields=()):
         self.handle = C.c_void_p(handle)
         self.batch = batch
         self.nts = list(nts)
+        self.fields = list(fields) or [False] * batch  # instance b has a viscosity field
 
     def close(self):
         if self.handle:
@@ -176,7 +177,8 @@ def mfg_plan(problems, precision=None):
     arr = (MfgProblem * len(structs))(*structs)
     h = C.c_void_p()
     _check(LIB.mfg_plan(arr, len(structs), C.byref(h)))
-    return Plan(h.value, len(problems), [d["nt"] for d in problems])
+    return Plan(h.value, len(problems), [d["nt"] for d in problems],
+                [d.get("nu_field") is not None for d in problems])
 
 
 def mfg_destroy(plan):
@@ -254,13 +256,15 @@ def mfg_solve_host(plan, m0, V, W, y, ybar, z, stats=None, stream=None):
 
 
 def mfg_adjoint(plan, b, y, z, gy, dm0, dV, dW, dnu, tol=1e-10, max_iter=5000, stream=None):
-    """Implicit-differentiation gradient at a converged solution (see mfg.h)."""
+    """Implicit-differentiation gradient at a converged solution (see mfg.h).
+    dnu: 1 element, or Nx*Ny (dloss/dnu(x)) for an instance with a viscosity field."""
     lay = mfg_layout(plan, b)
     n, cn = lay["n"], lay["n"] * lay["c"]
     S = n // plan_nt(plan, b)
     st = MfgStats()
+    field = plan.fields[b] if b < len(plan.fields) else False
     rc = LIB.mfg_adjoint(plan.handle, b, _ptr(y, cn), _ptr(z, n), _ptr(gy, cn), _ptr(dm0, S), _ptr(dV, S),
-                         _ptr(dW, S) if dW is not None else C.c_void_p(), _ptr(dnu, 1), float(tol),
+                         _ptr(dW, S) if dW is not None else C.c_void_p(), _ptr(dnu, S if field else 1), float(tol),
                          int(max_iter), C.byref(st), _stream(stream))
     if rc not in (MFG_OK, MFG_ERR_NOT_CONVERGED):
         _check(rc)

@@ -8,7 +8,10 @@
 // and the same preconditioner P as the forward solve, then
 // mu = H^{-1} (g - C^T eta).  Gradients (dloss/dtheta = -[mu; eta].dR/dtheta):
 //   dm0(x) = eta(0, x)/dt,  dV(x) = -sum_k mu_m(k, x),  dW(x) = -mu_m(N_t-1, x)/dt,
-//   dnu = -sum mu_m (K z) - sum eta (K m).
+//   dnu = -sum mu_m (K z) - sum eta (K m);
+// with a viscosity field, K_nu in C and, per node a (dK_nu/dnu_a = sum over
+// the faces f of a of g_f g_f^T / (2 dx^2), g_f the face difference),
+//   dnu(a) = -(1/2) sum_k sum_{f of a} [(g_f.mu_m)(g_f.z) + (g_f.eta)(g_f.m)] / dx^2.
 //
 // H^{-1} per cell in closed form.  With a' = f_eff'(m) (f_a + 2 f_b m, plus
 // g_a/dt on the last plane), H = [[|w|^2/m^3 + a', -w^T/m^2], [-w/m^2, I/m]]
@@ -67,8 +70,9 @@ __global__ void __launch_bounds__(kThreads) k_hinv(Geom g, Coef cf, const double
   }
 }
 
-// out = H^{-1} (C^T p)  or, with gsub, out = H^{-1} (gsub - C^T p).
-template <int ACTX>
+// out = H^{-1} (C^T p)  or, with gsub, out = H^{-1} (gsub - C^T p).  VN: L =
+// K_nu + I/dt with the face coefficients of Geom::kfx / kfy.
+template <int ACTX, bool VN>
 __global__ void __launch_bounds__(kThreads) k_ct_hinv(Geom g, Coef cf, const double* __restrict__ y,
                                                       const double* __restrict__ p,
                                                       const double* __restrict__ gsub,
@@ -89,14 +93,20 @@ __global__ void __launch_bounds__(kThreads) k_ct_hinv(Geom g, Coef cf, const dou
     const int jm = hmy ? (j == 0 ? g.ny - 1 : j - 1) : j;
     const int jp = hpy ? (j == g.ny - 1 ? 0 : j + 1) : j;
     const double pjm = p[rowi + jm], pjp = p[rowi + jp];
-    double Kp = g.ay * ((hmy ? pc - pjm : 0.0) + (hpy ? pc - pjp : 0.0));
+    const long long f0 = (long long)i * g.ny;
+    // K_nu p: a missing face has its neighbour index at the node itself (difference 0)
+    double Kp = VN ? fma(g.kfy[f0 + j], pc - pjp, g.kfy[f0 + jm] * (pc - pjm))
+                   : g.ay * ((hmy ? pc - pjm : 0.0) + (hpy ? pc - pjp : 0.0));
     double xw[NW];
     if (ACTX) {
       const bool hmx = g.perx || i >= 1, hpx = g.perx || i <= g.nx - 2;
       const int im = hmx ? (i == 0 ? g.nx - 1 : i - 1) : i;
       const int ip = hpx ? (i == g.nx - 1 ? 0 : i + 1) : i;
       const double pim = p[base + (long long)im * g.ny + j], pip = p[base + (long long)ip * g.ny + j];
-      Kp += g.ax * ((hmx ? pc - pim : 0.0) + (hpx ? pc - pip : 0.0));
+      if (VN)
+        Kp = fma(g.kfx[f0 + j], pc - pip, fma(g.kfx[(long long)im * g.ny + j], pc - pim, Kp));
+      else
+        Kp += g.ax * ((hmx ? pc - pim : 0.0) + (hpx ? pc - pip : 0.0));
       xw[0] = hpx ? (pc - pip) * g.idx : 0.0;
       xw[1] = hmx ? (pim - pc) * g.idx : 0.0;
       xw[2] = hpy ? (pc - pjp) * g.idy : 0.0;
@@ -106,7 +116,7 @@ __global__ void __launch_bounds__(kThreads) k_ct_hinv(Geom g, Coef cf, const dou
       xw[1] = hmy ? (pjm - pc) * g.idy : 0.0;
     }
     const double pn = (k + 1 < g.nt) ? p[e + g.S] : 0.0;
-    double xm = g.nu * Kp + (pc - pn) * g.idt;
+    double xm = (VN ? Kp : g.nu * Kp) + (pc - pn) * g.idt;
     if (gsub != nullptr) {
       xm = gsub[e] - xm;
 #pragma unroll
@@ -122,7 +132,9 @@ __global__ void __launch_bounds__(kThreads) k_ct_hinv(Geom g, Coef cf, const dou
   }
 }
 
-// One thread per spatial point, looping over time planes; dnu by reduction.
+// One thread per spatial point, looping over time planes; dnu by reduction,
+// or (VN) the node derivative dnu(f) written per point.
+template <bool VN>
 __global__ void __launch_bounds__(kThreads) k_adj_grads(Geom g, const double* __restrict__ y,
                                                         const double* __restrict__ z,
                                                         const double* __restrict__ eta,
@@ -139,25 +151,41 @@ __global__ void __launch_bounds__(kThreads) k_adj_grads(Geom g, const double* __
     const bool hmx = g.actx && (g.perx || i >= 1), hpx = g.actx && (g.perx || i <= g.nx - 2);
     const int im = hmx ? (i == 0 ? g.nx - 1 : i - 1) : i;
     const int ip = hpx ? (i == g.nx - 1 ? 0 : i + 1) : i;
-    double sv = 0.0;
+    double sv = 0.0, node = 0.0;
     for (int k = 0; k < g.nt; ++k) {
       const long long base = (long long)k * g.S;
       const long long e = base + f;
-      auto K5 = [&](const double* a) {
-        const double c = a[e];
-        return g.ay * ((hmy ? c - a[base + (long long)i * g.ny + jm] : 0.0) +
-                       (hpy ? c - a[base + (long long)i * g.ny + jp] : 0.0)) +
-               g.ax * ((hmx ? c - a[base + (long long)im * g.ny + j] : 0.0) +
-                       (hpx ? c - a[base + (long long)ip * g.ny + j] : 0.0));
-      };
       const double mum = mu[e];
       sv += mum;
-      acc -= mum * K5(z) + eta[e] * K5(y);
+      if (VN) {
+        // the node's faces: (g.mu)(g.z) + (g.eta)(g.m) per face, times 1/dx^2
+        auto face = [&](long long nb, double c) {
+          const double a = (mum - mu[nb]) * (z[e] - z[nb]) + (eta[e] - eta[nb]) * (y[e] - y[nb]);
+          return c * a;
+        };
+        double t = 0.0;
+        if (hmy) t += face(base + (long long)i * g.ny + jm, g.ay);
+        if (hpy) t += face(base + (long long)i * g.ny + jp, g.ay);
+        if (hmx) t += face(base + (long long)im * g.ny + j, g.ax);
+        if (hpx) t += face(base + (long long)ip * g.ny + j, g.ax);
+        node += t;
+      } else {
+        auto K5 = [&](const double* a) {
+          const double c = a[e];
+          return g.ay * ((hmy ? c - a[base + (long long)i * g.ny + jm] : 0.0) +
+                         (hpy ? c - a[base + (long long)i * g.ny + jp] : 0.0)) +
+                 g.ax * ((hmx ? c - a[base + (long long)im * g.ny + j] : 0.0) +
+                         (hpx ? c - a[base + (long long)ip * g.ny + j] : 0.0));
+        };
+        acc -= mum * K5(z) + eta[e] * K5(y);
+      }
     }
+    if (VN) dnu[f] = -0.5 * node;
     dm0[f] = eta[f] * g.idt;
     dV[f] = -sv;
     if (dW != nullptr) dW[f] = -mu[(long long)(g.nt - 1) * g.S + f] * g.idt;
   }
+  if (VN) return;
   double part[1] = {acc};
   block_sum<1>(part);
   if (!publish_and_check_last<1>(part, partials, &sc->counter)) return;
@@ -181,17 +209,25 @@ void launch_hinv(const Geom& g, const Coef& cf, const double* y, const double* u
 void launch_ct_hinv(const Geom& g, const Coef& cf, const double* y, const double* p,
                     const double* gsub, double* out, cudaStream_t s, const DevScalars* sc) {
   const int nb = red_blocks(g.n, g.vec_blocks);
-  if (g.actx)
-    k_ct_hinv<1><<<nb, kThreads, 0, s>>>(g, cf, y, p, gsub, out, sc);
+  const bool vn = g.kfy != nullptr;
+  if (g.actx && vn)
+    k_ct_hinv<1, true><<<nb, kThreads, 0, s>>>(g, cf, y, p, gsub, out, sc);
+  else if (g.actx)
+    k_ct_hinv<1, false><<<nb, kThreads, 0, s>>>(g, cf, y, p, gsub, out, sc);
+  else if (vn)
+    k_ct_hinv<0, true><<<nb, kThreads, 0, s>>>(g, cf, y, p, gsub, out, sc);
   else
-    k_ct_hinv<0><<<nb, kThreads, 0, s>>>(g, cf, y, p, gsub, out, sc);
+    k_ct_hinv<0, false><<<nb, kThreads, 0, s>>>(g, cf, y, p, gsub, out, sc);
 }
 
 void launch_adj_grads(const Geom& g, const double* y, const double* z, const double* eta,
                       const double* mu, double* dm0, double* dV, double* dW, double* dnu,
                       double* partials, DevScalars* sc, cudaStream_t s) {
   const int nb = red_blocks(g.S, g.vec_blocks);
-  k_adj_grads<<<nb, kThreads, 0, s>>>(g, y, z, eta, mu, dm0, dV, dW, dnu, partials, sc);
+  if (g.kfy != nullptr)
+    k_adj_grads<true><<<nb, kThreads, 0, s>>>(g, y, z, eta, mu, dm0, dV, dW, dnu, partials, sc);
+  else
+    k_adj_grads<false><<<nb, kThreads, 0, s>>>(g, y, z, eta, mu, dm0, dV, dW, dnu, partials, sc);
 }
 
 }  // namespace mfg

@@ -803,8 +803,6 @@ int mfg_adjoint(mfg_plan_t pl, int b, const double* y, const double* z, const do
   Inst& in = pl->inst[b];
   if (in.p.qprime != 2.0)
     return fail(MFG_ERR_UNSUPPORTED, "the adjoint is built for the quadratic Hamiltonian (q' = 2) only");
-  if (pl->inst[b].g.kfy != nullptr)
-    return fail(MFG_ERR_UNSUPPORTED, "the adjoint is built for a constant viscosity only");
   const Geom& g = in.g;
   const size_t n = (size_t)g.n;
   if (!in.adj_t) {

@@ -14,7 +14,8 @@ per-frequency systems of Alg. 1, Sec. 4.1).
     inexact solve, counting PCG iterations;
   - a field instance batched with a constant-nu one (bitwise equal to the solo
     solves), both stop references and the adaptive PCG rule, general q';
-  - the adjoint refuses a field (MFG_ERR_UNSUPPORTED)."""
+  - the adjoint with a field (node derivatives dloss/dnu(x)) against the
+    oracle's KKT gradient, directly and through torch.autograd."""
 import numpy as np
 import pytest
 
@@ -259,16 +260,70 @@ def test_field_general_hamiltonian():
     assert rel(y, ref["y"]) <= max(1e-8, 10.0 * _field_cond(inst["problem"]) * 2.0 ** -53)
 
 
-def test_field_adjoint_is_unsupported():
+def _field_converged(case, precision, iters=3000):
     import torch
-    inst = _inst(CASES[0])
+    inst = mi.small(**case, eps=0.0)
+    p = dict(inst["problem"], gamma=0.05, max_cp=iters, cg_tol=1e-12, precision=precision)
+    p["nu_field"] = mi.viscosity_field(p, p["nu"], 4.0, case["seed"] + 3, "smooth")
+    rng = np.random.default_rng(case["seed"])
+    nx, ny = p["n"]
+    m0 = mi._normalise(1.0 + 0.3 * rng.uniform(size=(nx, ny)), p)
+    V = 0.3 * rng.normal(size=(nx, ny))
+    W = 0.2 * rng.normal(size=(nx, ny))
+    mt = mi._normalise(1.0 + 0.3 * rng.uniform(size=(nx, ny)), p)
     L = lib()
-    plan = L.mfg_plan(dict(inst["problem"], max_cp=2))
-    s, n, c = ops.sizes(inst["problem"])
-    y = dev(inst["y0"])
-    z = torch.zeros(n, dtype=torch.float64, device="cuda")
-    out = torch.zeros(s, dtype=torch.float64, device="cuda")
-    dnu = torch.zeros(1, dtype=torch.float64, device="cuda")
-    with pytest.raises(L.MfgError) as e:
-        L.mfg_adjoint(plan, 0, y, z, torch.zeros_like(y), out, out.clone(), out.clone(), dnu)
-    assert e.value.code == L.MFG_ERR_UNSUPPORTED
+    plan = L.mfg_plan(p)
+    y = dev(mi.initial_iterate(p, m0))
+    ybar = y.clone()
+    z = torch.zeros(ops.sizes(p)[1], dtype=torch.float64, device="cuda")
+    rc, st = L.mfg_solve(plan, dev(m0), dev(V), dev(W), y, ybar, z)
+    assert rc == 0
+    return p, plan, m0, V, W, mt, y, z
+
+
+ADJ_CASES = [dict(seed=61, dim=2, nx=12, ny=10, nt=6, bc=("periodic", "periodic"), nu=0.2),
+             dict(seed=62, dim=2, nx=9, ny=14, nt=5, bc=("neumann", "periodic"), nu=0.05),
+             dict(seed=63, dim=1, nx=40, nt=8, bc=("neumann", "neumann"), nu=0.1)]
+
+
+@pytest.mark.parametrize("case", ADJ_CASES)
+@pytest.mark.parametrize("precision", ["fp64", "mixed_tc"])
+def test_field_adjoint_matches_oracle_kkt(case, precision):
+    """The adjoint with a field (banded P inside the Schur PCG, K_nu in C^T,
+    node derivatives dloss/dnu(x)) against the oracle's sparse-LU KKT gradient,
+    itself pinned by central differences (tests/test_oracle_varnu.py)."""
+    import torch
+    from oracle import adjoint as oadj
+    p, plan, m0, V, W, mt, y, z = _field_converged(case, precision)
+    yh, zh = host(y).reshape((1 + 2 * p["dim"], p["nt"]) + tuple(p["n"])), host(z)
+    _, g = oadj.loss_mT(p, yh, mt)
+    ref = oadj.adjoint_gradients(p, yh, zh.reshape(p["nt"], *p["n"]), g)
+    S = p["n"][0] * p["n"][1]
+    dm0, dV, dW, dnu = (torch.empty(S, dtype=torch.float64, device="cuda") for _ in range(4))
+    rc, st = lib().mfg_adjoint(plan, 0, y, z, dev(g), dm0, dV, dW, dnu, tol=1e-12)
+    assert rc == 0 and st.status == 0 and st.cg_iters > 0
+    for got, key in ((dm0, "dm0"), (dV, "dV"), (dW, "dW"), (dnu, "dnu")):
+        assert rel(host(got), ref[key]) <= 1e-7, key
+
+
+def test_field_autograd_gradient():
+    """torch.autograd through a field: the (Nx, Ny) nu tensor gets the node
+    derivatives of the direct call."""
+    import torch
+    from oracle import adjoint as oadj
+    from paper_2507_01958_gb300.autograd import equilibrium_mT
+    case = ADJ_CASES[0]
+    p, plan, m0, V, W, mt, y, z = _field_converged(case, "fp64")
+    nu = torch.as_tensor(np.asarray(p["nu_field"]), dtype=torch.float64, device="cuda").requires_grad_(True)
+    m0t = dev(m0).reshape(p["n"]).requires_grad_(True)
+    q = {k: v for k, v in p.items() if k != "nu_field"}
+    mT = equilibrium_mT(m0t, dev(V).reshape(p["n"]), dev(W).reshape(p["n"]), nu, q, "fp64", 1e-12)
+    dx, dy = ops.spacing(p)
+    loss = ((mT - dev(mt).reshape(p["n"])) ** 2).sum() * dx * dy
+    loss.backward()
+    yh = host(y).reshape((5, p["nt"]) + tuple(p["n"]))
+    _, g = oadj.loss_mT(p, yh, mt)
+    ref = oadj.adjoint_gradients(p, yh, host(z).reshape(p["nt"], *p["n"]), g)
+    assert nu.grad.shape == tuple(p["n"])
+    assert rel(host(nu.grad), ref["dnu"]) <= 1e-7
+    assert rel(host(m0t.grad), ref["dm0"]) <= 1e-7
