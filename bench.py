@@ -567,10 +567,13 @@ def run_gpu(args):  # noqa: C901
     host_step(start_iterate())  # first call allocates the plan's staging buffers
     sets = [start_iterate() for _ in range(e2e_steps)]
     torch.cuda.synchronize()
+    e2e_clocks = ClockSampler(local)
+    e2e_clocks.start()
     h0 = time.perf_counter()
     for i in range(e2e_steps):
         st = host_step(sets[i])
     h1 = time.perf_counter()
+    e2e_clk = e2e_clocks.stop()
     del sets
     t_e2e = reduce_max(h1 - h0, world, dev)
     cp_e2e = reduce_sum(float(sum(s.cp_iters for s in st) * e2e_steps), world, dev)
@@ -663,7 +666,7 @@ def run_gpu(args):  # noqa: C901
                          "hbm_peak_gbs": peaks.get("hbm_gbs"), "peak_source": f"{src} (HBM); recipe table (FP64)"},
             "cpu_baseline": cpu,
             "e2e": {"value": cp_e2e / t_e2e, "unit": "CP iterations/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps, "clocks": e2e_clk},
             "gpu_launches": int(launches),
             "clocks": clk,
             "schedule": schedule,
