@@ -507,6 +507,11 @@ def run_gpu(args):  # noqa: C901
     L = pkg.lib()
     stream = torch.cuda.current_stream(dev)
     inst, p = headline_problem(args.precision, cp=args.cp_per_step)
+    if args.small:
+        if not args.quick:
+            raise SystemExit("--small applies to --kernels-only and --quick runs only")
+        inst = mi.config3(nt=32)  # 512^2 x 32: a profiling case, not a benchmark number
+        p = dict(inst["problem"], max_cp=args.cp_per_step, cg_tol=CG_TOL, precision=args.precision)
     main = Fixed(L, dev, [inst], [p], stream)
     if not args.no_autotune:
         L.mfg_autotune(main.plan, stream=stream)
@@ -763,7 +768,8 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true", help="skip the extra measurements after the headline")
     ap.add_argument("--kernels-only", action="store_true",
                     help="three launches of each standalone hot kernel (for ncu captures)")
-    ap.add_argument("--small", action="store_true", help="--kernels-only on the 512^2 x 32 Neumann grid")
+    ap.add_argument("--small", action="store_true",
+                    help="--kernels-only or --quick on the 512^2 x 32 Neumann grid (profiling runs)")
     ap.add_argument("--field", action="store_true",
                     help="--kernels-only on the viscosity-field workload (banded preconditioner)")
     ap.add_argument("--no-autotune", action="store_true",

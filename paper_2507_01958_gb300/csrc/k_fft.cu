@@ -233,8 +233,13 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
         const int m = k * (N / (8 * Ns));
         cx<T> a[8];
         a[0] = src[swz<N>(j)];
+        if (st == 0) {  // Ns = 1: every twiddle is 1
 #pragma unroll
-        for (int r = 1; r < 8; ++r) a[r] = cmul(src[swz<N>(j + r * (N / 8))], twid(r * m));
+          for (int r = 1; r < 8; ++r) a[r] = src[swz<N>(j + r * (N / 8))];
+        } else {
+#pragma unroll
+          for (int r = 1; r < 8; ++r) a[r] = cmul(src[swz<N>(j + r * (N / 8))], twid(r * m));
+        }
         // 8-point DFT: even and odd 4-point DFTs, then A_s = E_s + w^s O_s,
         // A_{s+4} = E_s - w^s O_s with w = exp(sgn 2 pi i / 8)
         dft4(a[0], a[2], a[4], a[6]);
@@ -262,9 +267,12 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
         const int k = j & (Ns - 1);
         const int m = k * (N / (4 * Ns));
         cx<T> a0 = src[swz<N>(j)];
-        cx<T> a1 = cmul(src[swz<N>(j + N / 4)], twid(m));
-        cx<T> a2 = cmul(src[swz<N>(j + N / 2)], twid(2 * m));
-        cx<T> a3 = cmul(src[swz<N>(j + 3 * N / 4)], twid(3 * m));
+        cx<T> a1 = src[swz<N>(j + N / 4)], a2 = src[swz<N>(j + N / 2)], a3 = src[swz<N>(j + 3 * N / 4)];
+        if (st > 0) {  // Ns = 1 (the first stage): every twiddle is 1
+          a1 = cmul(a1, twid(m));
+          a2 = cmul(a2, twid(2 * m));
+          a3 = cmul(a3, twid(3 * m));
+        }
         dft4(a0, a1, a2, a3);
         const int d = ((j - k) << 2) + k;
         dst[swz<N>(d)] = a0;
@@ -315,12 +323,14 @@ __global__ void __launch_bounds__(256) k_fft(const TI* __restrict__ in, TO* __re
   const T rsn = T(1) / sqrt(T(N));
   for (int idx = tid; idx < CL * N; idx += 256) {
     const int q = idx / N, k = idx % N;
-    const cx<T> zk = Z[q * NP + swz<N>(k)];
     if (MODE == FFT_DCT3) {
-      const int pos = (k < N / 2) ? 2 * k : 2 * (N - 1 - k) + 1;
-      R[(2 * q) * NP + pos] = zk.x;
-      R[(2 * q + 1) * NP + pos] = zk.y;
+      // x_{2n} = v_n, x_{2n+1} = v_{N-1-n}: walk the output position (k here)
+      // so that the stores are contiguous; read v at the matching index
+      const cx<T> zv = Z[q * NP + swz<N>((k & 1) ? N - 1 - (k >> 1) : (k >> 1))];
+      R[(2 * q) * NP + k] = zv.x;
+      R[(2 * q + 1) * NP + k] = zv.y;
     } else {
+      const cx<T> zk = Z[q * NP + swz<N>(k)];
       const cx<T> zm = Z[q * NP + swz<N>((N - k) & (N - 1))];
       const T sr = T(0.5) * (zk.x + zm.x), si = T(0.5) * (zk.y - zm.y);  // X_a
       const T dr = T(0.5) * (zk.y + zm.y), di = T(0.5) * (zm.x - zk.x);  // X_b
