@@ -85,7 +85,7 @@ typedef struct {
   int bc[2];         /* MFG_PERIODIC | MFG_NEUMANN per axis (Alg. 2 allows mixed)    */
   int nt;            /* N_t >= 2 time steps                                           */
   double T;          /* horizon T > 0, dt = T/N_t                                      */
-  double nu;         /* viscosity nu >= 0                                              */
+  double nu;         /* viscosity nu >= 0 (ignored when nu_field is set)               */
   double qprime;     /* Hamiltonian exponent q' of eq. power_hamiltonian, in [1.05, 20];
                         2 takes the fast prox, others a general FP64 root finder    */
   double f_a, f_b;   /* f(x,m) = f_a m + f_b m^2 + V(x); f_a, f_b >= 0 (monotone f)   */

@@ -382,18 +382,28 @@ int time_tc_configure() {
                               (int)TcShape<64>::smem) != cudaSuccess;
   bad |= cudaFuncSetAttribute(k_time_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)TcShape<128>::smem) != cudaSuccess;
-  int occ[3] = {1, 1, 1};
-  bad |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_time_tc<32>, kTcThreads, TcShape<32>::smem) !=
-         cudaSuccess;
-  bad |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_time_tc<64>, kTcThreads, TcShape<64>::smem) !=
-         cudaSuccess;
-  bad |= cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_time_tc<128>, kTcThreads, TcShape<128>::smem) !=
-         cudaSuccess;
+  // Resident blocks per SM from the kernel's own attributes: registers (in
+  // their allocation unit of 8 per thread), shared memory (dynamic + static +
+  // the 1 KB the driver reserves per block) and tensor-memory columns.  (The
+  // occupancy API reported 1 block for the N_t = 32 kernel, whose registers
+  // and shared memory admit 2 and 3; the blocks are independent, so a grid of
+  // what fits is safe either way.)
+  int dev = 0, smem_sm = 0, regs_sm = 0;
+  bad |= cudaGetDevice(&dev) != cudaSuccess;
+  bad |= cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess;
+  bad |= cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess;
+  const void* fns[3] = {(const void*)k_time_tc<32>, (const void*)k_time_tc<64>, (const void*)k_time_tc<128>};
+  const size_t smem[3] = {TcShape<32>::smem, TcShape<64>::smem, TcShape<128>::smem};
   const int cols[3] = {64, 128, 256};
   for (int i = 0; i < 3; ++i) {
-    int b = occ[i] < 1 ? 1 : occ[i];
+    cudaFuncAttributes fa{};
+    bad |= cudaFuncGetAttributes(&fa, fns[i]) != cudaSuccess;
+    const int regs = ((fa.numRegs + 7) / 8) * 8 * kTcThreads;
+    int b = regs > 0 ? regs_sm / regs : 1;
+    const int by_smem = (int)((size_t)smem_sm / (smem[i] + fa.sharedSizeBytes + 1024));
+    if (by_smem < b) b = by_smem;
     if (b * cols[i] > 512) b = 512 / cols[i];
-    g_tc_blocks_per_sm[i] = b;
+    g_tc_blocks_per_sm[i] = b < 1 ? 1 : b;
   }
   return bad ? MFG_ERR_CUDA : MFG_OK;
 }
