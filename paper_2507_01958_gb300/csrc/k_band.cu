@@ -32,8 +32,8 @@ namespace mfg {
 
 namespace {
 
-constexpr int kBandRing = 4;           // shared-memory stages of factor rows
-constexpr int kBandStageBytes = 45 * 1024;
+constexpr int kBandRing = 5;           // shared-memory stages of factor rows
+constexpr int kBandStageBytes = 40 * 1024;
 constexpr int kBandMaxW = 4096;
 constexpr double kBandMaxBytes = 64.0 * 1024 * 1024 * 1024;
 
@@ -128,9 +128,11 @@ int band_row_words(int w, size_t elt) {
   return (w + 1 + per16 - 1) / per16 * per16;
 }
 
-// Launch shape of the substitutions.  G: the block of steps, the largest power
-// of two <= 32 whose stage (G factor rows, plus the G x G inverse of the
-// block's triangle when G >= 4) fits in kBandStageBytes, at least 1.
+// Launch shape of the substitutions.  G, the block of steps: the largest power
+// of two <= 32 with 2G <= w (the pipelined schedule below needs the next
+// block inside the band) whose stage (G factor rows, plus the G x G inverse of
+// the block's triangle when G >= 4) fits in kBandStageBytes.  The half-width
+// w is at least 2 (padded with zero coefficients), so G = 1 always fits.
 struct BandShape {
   int wp, G, inv, stage, threads;
   size_t smem;
@@ -142,31 +144,39 @@ BandShape band_shape(int w) {
   b.wp = band_row_words(w, sizeof(T));
   auto stage = [&](int G) { return G * b.wp + (G >= 4 ? G * G : 0); };
   b.G = 1;
-  while (b.G < 32 && (size_t)stage(b.G * 2) * sizeof(T) <= (size_t)kBandStageBytes) b.G *= 2;
+  while (b.G < 32 && 4 * b.G <= w && (size_t)stage(b.G * 2) * sizeof(T) <= (size_t)kBandStageBytes) b.G *= 2;
   b.inv = b.G >= 4;
   b.stage = stage(b.G);
-  b.threads = std::min(512, std::max(32, (w + 31) / 32 * 32));
-  b.smem = sizeof(T) * ((size_t)kBandRing * b.stage + (size_t)kBandRing * b.G + 32 + (size_t)w + b.G);
+  // warp 0 solves the blocks; warps 1.. take the w - G far entries
+  b.threads = std::min(512, std::max(64, 32 + (w - b.G + 31) / 32 * 32));
+  const size_t rg = ((size_t)kBandRing * b.G + 3) / 4 * 4;
+  b.smem = sizeof(T) * ((size_t)kBandRing * b.stage + rg + 64 + (size_t)w + b.G);
   return b;
 }
 
+// Factor rows in step order (the order the substitutions consume them),
+// padded to a whole number of blocks: step t of the forward solve L y = b is
+// band row t, with row (1/L_tt, L_{t+1,t}, ..., L_{t+w,t}); step t of the
+// backward solve L^T x = y is band row j = S-1-t, with row (1/L_jj, L_{j,j-1},
+// ..., L_{j,j-w}).  Entry d of a row couples step t to step t + d.  Padding
+// steps (t >= S) carry 1/L = 1 and no coupling.  For G >= 4 every block also
+// stores the transposed inverse of its G x G step-space triangle.
 template <typename T>
 int build_factors(const Geom& g, const std::vector<Row>& chat, const std::vector<Row>& lhat,
                   const std::vector<int>& ipos, const double* lamt, int w, PrecTables* t,
                   std::string* err) {
   const int S = g.S, nt = g.nt;
-  const int wp = band_row_words(w, sizeof(T));
-  const size_t per = (size_t)S * wp;
-  std::vector<T> Lc(per * nt, T(0)), Lr(per * nt, T(0));
-  std::vector<int> bad((size_t)nt, 0);
-  // inverses of the full blocks' step-space triangles, per direction:
-  // Dinv[(k nblk + blk) G^2 + b G + a] = (T_blk^{-1})[a][b]
   const BandShape bs = band_shape<T>(w);
-  const int G = bs.G, nblk = bs.inv ? S / G : 0;
-  const size_t perD = (size_t)nblk * G * G;
+  const int G = bs.G, wp = bs.wp;
+  const int Sp = (S + G - 1) / G * G, nblk = Sp / G;
+  const size_t per = (size_t)Sp * wp;
+  const size_t perD = bs.inv ? (size_t)nblk * G * G : 0;
+  std::vector<T> Fc(per * nt, T(0)), Fr(per * nt, T(0));
   std::vector<T> Dc(perD * nt, T(0)), Dr(perD * nt, T(0));
+  std::vector<int> bad((size_t)nt, 0);
   auto work = [&](int k0, int k1) {
     std::vector<double> A((size_t)S * (w + 1));
+    std::vector<double> Tm((size_t)G * G), Ti((size_t)G * G);
     for (int k = k0; k < k1; ++k) {
       std::fill(A.begin(), A.end(), 0.0);
       for (int a = 0; a < S; ++a) {
@@ -185,25 +195,35 @@ int build_factors(const Geom& g, const std::vector<Row>& chat, const std::vector
         bad[(size_t)k] = 1;
         continue;
       }
-      // Step-space triangle of block blk (steps t0 .. t0+G-1): Tm[a][b] couples
-      // step t0+b to step t0+a at distance a - b (0 beyond w), the diagonal
-      // holds L_jj.  Forward: step t is band row t and the coupling is
-      // L_{t0+a, t0+b}; backward: step t is band row S-1-t and the coupling is
-      // L_{S-1-t0-b, S-1-t0-a}.  Inverted by forward substitution in FP64.
-      std::vector<double> Tm((size_t)G * G), Ti((size_t)G * G);
-      for (int dir = 0; dir < 2 && nblk > 0; ++dir) {
+      // coupling of step tt to step tt + d in direction dir, 0 outside the matrix
+      auto coef = [&](int dir, int tt, int d) -> double {
+        if (tt >= S || tt + d >= S) return 0.0;
+        const int col = dir == 0 ? tt : S - 1 - tt - d;  // column of L in band storage
+        return A[(size_t)col * (w + 1) + d];
+      };
+      auto diag = [&](int dir, int tt) -> double {
+        if (tt >= S) return 1.0;
+        return A[(size_t)(dir == 0 ? tt : S - 1 - tt) * (w + 1)];
+      };
+      for (int dir = 0; dir < 2; ++dir) {
+        T* F = (dir == 0 ? Fc.data() : Fr.data()) + per * k;
+        for (int tt = 0; tt < Sp; ++tt) {
+          F[(size_t)tt * wp] = (T)(1.0 / diag(dir, tt));
+          for (int d = 1; d <= w; ++d) F[(size_t)tt * wp + d] = (T)coef(dir, tt, d);
+        }
+        if (!bs.inv) continue;
+        // Step-space triangle of each block (steps t0 .. t0+G-1), inverted by
+        // forward substitution in FP64, stored transposed.
         T* D = (dir == 0 ? Dc.data() : Dr.data()) + perD * k;
         for (int blk = 0; blk < nblk; ++blk) {
           const int t0 = blk * G;
           std::fill(Tm.begin(), Tm.end(), 0.0);
-          for (int a = 0; a < G; ++a)
-            for (int b = 0; b <= a; ++b) {
-              const int d = a - b;
-              if (d > w) continue;
-              const int col = dir == 0 ? t0 + b : S - 1 - t0 - a;  // column of L in band storage
-              Tm[(size_t)a * G + b] = A[(size_t)col * (w + 1) + d];
-            }
-          for (int c = 0; c < G; ++c)  // column c of the inverse
+          for (int a = 0; a < G; ++a) {
+            Tm[(size_t)a * G + a] = diag(dir, t0 + a);
+            for (int b = 0; b < a; ++b)
+              if (a - b <= w) Tm[(size_t)a * G + b] = coef(dir, t0 + b, a - b);
+          }
+          for (int c = 0; c < G; ++c)
             for (int a = 0; a < G; ++a) {
               double v = (a == c) ? 1.0 : 0.0;
               for (int b = c; b < a; ++b) v -= Tm[(size_t)a * G + b] * Ti[(size_t)b * G + c];
@@ -212,17 +232,6 @@ int build_factors(const Geom& g, const std::vector<Row>& chat, const std::vector
           T* Db = D + (size_t)blk * G * G;
           for (int a = 0; a < G; ++a)
             for (int b = 0; b < G; ++b) Db[(size_t)b * G + a] = (T)Ti[(size_t)a * G + b];
-        }
-      }
-      T* lc = Lc.data() + per * k;
-      T* lr = Lr.data() + per * k;
-      for (int j = 0; j < S; ++j) {
-        const double* cj = &A[(size_t)j * (w + 1)];
-        lc[(size_t)j * wp] = (T)(1.0 / cj[0]);
-        lr[(size_t)j * wp] = (T)(1.0 / cj[0]);
-        for (int e = 1; e <= w; ++e) {
-          if (j + e < S) lc[(size_t)j * wp + e] = (T)cj[e];                             // L_{j+e, j}
-          if (j - e >= 0) lr[(size_t)j * wp + e] = (T)A[(size_t)(j - e) * (w + 1) + e];  // L_{j, j-e}
         }
       }
     }
@@ -236,10 +245,10 @@ int build_factors(const Geom& g, const std::vector<Row>& chat, const std::vector
       *err = "viscosity field: a per-frequency system is not positive definite";
       return MFG_ERR_INVALID_ARG;
     }
-  T* dc = upload_vec(Lc);
-  T* dr = upload_vec(Lr);
-  T* ic = nblk > 0 ? upload_vec(Dc) : nullptr;
-  T* ir = nblk > 0 ? upload_vec(Dr) : nullptr;
+  T* dc = upload_vec(Fc);
+  T* dr = upload_vec(Fr);
+  T* ic = bs.inv ? upload_vec(Dc) : nullptr;
+  T* ir = bs.inv ? upload_vec(Dr) : nullptr;
   if constexpr (sizeof(T) == 8) {
     t->bandc64 = dc;
     t->bandr64 = dr;
@@ -251,7 +260,7 @@ int build_factors(const Geom& g, const std::vector<Row>& chat, const std::vector
     t->bandic32 = ic;
     t->bandir32 = ir;
   }
-  if (!dc || !dr || (nblk > 0 && (!ic || !ir))) {
+  if (!dc || !dr || (bs.inv && (!ic || !ir))) {
     *err = "cudaMalloc failed for the banded factors";
     return MFG_ERR_CUDA;  // the caller frees what was uploaded
   }
@@ -306,7 +315,7 @@ int build_band_tables(const mfg_problem& p, const Geom& g, const double* lamt, P
     l.add(a, idt * idt);
     for (int q = 0; q < c.n; ++q) w = std::max(w, std::abs(ipos[(size_t)c.col[q]] - ipos[(size_t)a]));
   }
-  w = std::max(w, 1);
+  w = std::max(w, 2);  // the pipelined substitutions need 2G <= w with G >= 1
   const size_t elt = p.precision == MFG_FP64 ? 8 : 4;
   const double bytes = 2.0 * g.nt * (double)S * band_row_words(w, elt) * elt;
   if (w > kBandMaxW || bytes > kBandMaxBytes) {
@@ -370,29 +379,6 @@ __global__ void __launch_bounds__(256) k_time_xf(const TI* __restrict__ in, TO* 
   }
 }
 
-// One banded substitution per frequency (blockIdx.x = k).  Both directions are
-// the same lower-triangular banded solve in step order t = 0..S-1:
-//   forward (BWD = false, L y = b): step t is band index j = t, and row j of
-//     the column layout (1/L_jj, then L_{j+d, j}, d = 1..w) couples step t to
-//     step t + d;
-//   backward (BWD = true, L^T x = y): step t is j = S-1-t, and row j of the
-//     row layout (1/L_jj, then L_{j, j-d}) again couples step t to step t + d.
-// Steps go in blocks of G (a power of two <= 32): warp 0 solves the block's
-// G x G triangle, for G >= 4 as one product with the triangle's inverse
-// (formed on the host in FP64 and streamed with the rows; lane a sums G
-// terms, no dependency chain), else with shuffles (lane b holds entry t0+b and
-// its row of the triangle in registers), then every thread
-// subtracts the block's contribution from one of the next w entries (a G-term
-// dot product out of shared memory): two barriers per G steps.  The window
-// keeps entry t at slot t mod (w+G); during a block it holds entries
-// t0 .. t0+G+w-1, and the slots of the G entries the block finishes take
-// entries t0+G+w .. t0+2G+w-1, read from b (no earlier step reaches them:
-// their distance is above w).  Factor rows and refill values of a block
-// arrive through a ring of kBandRing shared-memory stages filled by cp.async
-// (16-byte chunks; 4- or 8-byte refill copies) kBandRing-1 blocks ahead;
-// cp.async.wait_group only waits for copies already issued, so the pipeline
-// cannot stall for good.  A last block shorter than G takes the same steps
-// with run-time bounds.
 // xr[0..G) = xs[0..G) with 16-byte shared loads (xs is 16-byte aligned)
 template <typename T, int G>
 __device__ __forceinline__ void load_block(const T* xs, T (&xr)[G]) {
@@ -415,146 +401,144 @@ __device__ __forceinline__ void load_block(const T* xs, T (&xr)[G]) {
   }
 }
 
+// One banded substitution per frequency (blockIdx.x = k).  Both directions are
+// the same lower-triangular banded solve in step order t = 0..S'-1 (S' = S
+// rounded up to whole blocks; padding steps have a unit diagonal, no coupling
+// and a zero right-hand side): row t of F holds 1/L_tt and the coefficients
+// coupling step t to steps t+1 .. t+w (forward: band row t of L; backward:
+// band row S-1-t of L^T).  Steps go in blocks of G (a power of two <= 32,
+// 2G <= w) with a one-block lag between the two kinds of work:
+//   warp 0 solves block st: its right-hand side is the window entry less
+//     `carry`, the contribution of block st-1 that warp 0 computed itself; the
+//     G x G triangle is one product with its inverse for G >= 4 (formed on the
+//     host in FP64 and streamed with the rows; lane a sums G terms, no
+//     dependency chain), else a shuffle chain; then it forms block st's
+//     contribution to block st+1 (distances G+l-b <= 2G-1 <= w) in `carry`;
+//   warps 1.. meanwhile subtract block st-1's contribution from entries
+//     t0+G .. t0+w-1 (distance 2G+e-b, zero past w) and copy the right-hand
+//     side of entries t0+w .. t0+w+G-1 into the window.
+// One barrier per block.  The window keeps entry t at slot t mod (w+G): during
+// block st it holds entries t0 .. t0+w+G-1, the new entries taking the slots
+// of block st-1, which nothing reads any more.  The solutions of blocks st and
+// st-1 sit in two halves of xs.  Factor rows, block inverses and right-hand
+// sides of a block arrive through a ring of kBandRing shared-memory stages
+// filled by cp.async (16-byte chunks; 4- or 8-byte right-hand-side copies)
+// kBandRing-2 blocks ahead, issued by warps 1..; stage st-1 is still read
+// during block st.  cp.async.wait_group only waits for copies already issued,
+// so the pipeline cannot stall for good.
 template <typename T, bool BWD, int G>
 __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T* __restrict__ sol,
                                                     const T* __restrict__ F, const T* __restrict__ Dinv,
                                                     int S, int w, int wp, const DevScalars* sc) {
-  constexpr bool INV = G >= 4;                    // full blocks carry their triangle's inverse
+  constexpr bool INV = G >= 4;                        // blocks carry their triangle's inverse
+  constexpr int RG = (kBandRing * G + 3) / 4 * 4;     // right-hand-side stages, 16-byte multiple
   if (sc != nullptr && sc->cg_done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int stage = G * wp + (INV ? G * G : 0);
-  T* ring = reinterpret_cast<T*>(smraw);          // kBandRing x (G x wp rows [+ G x G inverse])
-  T* refill = ring + (size_t)kBandRing * stage;   // kBandRing x G
-  T* xs = refill + (size_t)kBandRing * G;         // the block's solution (32)
-  T* win = xs + 32;                               // w + G
+  T* ring = reinterpret_cast<T*>(smraw);              // kBandRing x (G rows of wp [+ G x G inverse])
+  T* refill = ring + (size_t)kBandRing * stage;       // kBandRing x G
+  T* xs = refill + RG;                                // 2 x 32
+  T* win = xs + 64;                                   // w + G
   const int k = blockIdx.x, tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int wt = tid - 32, wn = nth - 32;             // rank among warps 1..
   const int W2 = w + G;
-  const T* Fk = F + (size_t)k * S * wp;
+  const int Sp = (S + G - 1) / G * G, nblk = Sp / G;
+  const T* Fk = F + (size_t)k * Sp * wp;
+  const T* Dk = INV ? Dinv + (size_t)k * nblk * G * G : nullptr;
   const T* bk = rhs + (size_t)k * S;
   T* xk = sol + (size_t)k * S;
-  const int nst = (S + G - 1) / G, nblk = S / G;
-  const T* Dk = INV ? Dinv + (size_t)k * nblk * G * G : nullptr;
   auto band = [&](int t) { return BWD ? S - 1 - t : t; };
   auto issue = [&](int st) {
-    if (st < nst) {
-      const int t0 = st * G, cnt = min(G, S - t0);
-      const int lo = BWD ? S - t0 - cnt : t0;  // lowest band row of the block
+    if (st < nblk && warp > 0) {
+      const int t0 = st * G;
       char* dst = reinterpret_cast<char*>(ring + (size_t)(st % kBandRing) * stage);
-      const char* g0 = reinterpret_cast<const char*>(Fk + (size_t)lo * wp);
-      const int chunks = (int)((size_t)cnt * wp * sizeof(T) / 16);
-      for (int c = tid; c < chunks; c += nth) cp_async16(dst + 16 * (size_t)c, g0 + 16 * (size_t)c);
-      if (INV && cnt == G) {
+      const char* g0 = reinterpret_cast<const char*>(Fk + (size_t)t0 * wp);
+      const int chunks = (int)((size_t)G * wp * sizeof(T) / 16);
+      for (int c = wt; c < chunks; c += wn) cp_async16(dst + 16 * (size_t)c, g0 + 16 * (size_t)c);
+      if constexpr (INV) {
         char* di = dst + (size_t)G * wp * sizeof(T);
         const char* gi = reinterpret_cast<const char*>(Dk + (size_t)st * G * G);
-        const int ci = (int)((size_t)G * G * sizeof(T) / 16);
-        for (int c = tid; c < ci; c += nth) cp_async16(di + 16 * (size_t)c, gi + 16 * (size_t)c);
+        constexpr int ci = (int)((size_t)G * G * sizeof(T) / 16);
+        for (int c = wt; c < ci; c += wn) cp_async16(di + 16 * (size_t)c, gi + 16 * (size_t)c);
       }
-      if (tid < cnt) {
-        const int r = t0 + w + G + tid;
-        if (r < S) cp_async_small<sizeof(T)>(refill + (st % kBandRing) * G + tid, bk + band(r));
+      if (wt < G) {
+        const int r = t0 + w + wt;
+        T* rf = refill + (st % kBandRing) * G + wt;
+        if (r < S)
+          cp_async_small<sizeof(T)>(rf, bk + band(r));
+        else
+          *rf = T(0);  // padding step
       }
     }
     cp_async_commit();
   };
-  for (int e = tid; e < W2 && e < S; e += nth) win[e] = bk[band(e)];
-  for (int st = 0; st < kBandRing - 1; ++st) issue(st);
+  for (int e = tid; e < w && e < Sp; e += nth) win[e] = e < S ? bk[band(e)] : T(0);
+  for (int st = 0; st < kBandRing - 2; ++st) issue(st);
   // slot of entry t0 + x is s0 + x, less W2 past the end (x < W2): no divisions
   int s0 = 0;
   auto slot = [&](int x) { const int q = s0 + x; return q >= W2 ? q - W2 : q; };
-  for (int st = 0; st < nst; ++st) {
-    cp_async_wait<kBandRing - 2>();
+  T carry = T(0);
+  const int ml = lane < G ? lane : 0;
+  for (int st = 0; st < nblk; ++st) {
+    cp_async_wait<kBandRing - 3>();
     __syncthreads();
-    issue(st + kBandRing - 1);
-    const int t0 = st * G, cnt = min(G, S - t0);
-    const int lo = BWD ? S - t0 - cnt : t0;
-    const T* rows = ring + (size_t)(st % kBandRing) * stage;
-    if (cnt == G) {
-      // factor row of step t0 + b inside the stage (compile-time index)
-#define ROW(b) (rows + (size_t)(BWD ? (G - 1 - (b)) : (b)) * wp)
-      if (INV) {
-        // x = T^{-1} acc with the block's precomputed inverse (transposed in
-        // the stage): G independent FMAs per lane, no dependency chain
-        if (warp == 0) {
-          const T* Di = rows + (size_t)G * wp;
-          const T accl = lane < G ? win[slot(lane)] : T(0);
-          const int ml = lane < G ? lane : 0;
-          T xa[4] = {T(0), T(0), T(0), T(0)};  // four independent FMA chains
+    issue(st + kBandRing - 2);
+    const int t0 = st * G;
+    const T* cur = ring + (size_t)(st % kBandRing) * stage;
+    if (warp == 0) {
+      T acc = lane < G ? win[slot(lane)] - carry : T(0);
+      T x = T(0);
+      if constexpr (INV) {
+        // x = T^{-1} acc with the block's inverse (transposed in the stage)
+        const T* Di = cur + (size_t)G * wp;
+        T xa[4] = {T(0), T(0), T(0), T(0)};  // four independent FMA chains
 #pragma unroll
-          for (int b = 0; b < G; ++b) xa[b & 3] = fma(Di[b * G + ml], __shfl_sync(0xffffffffu, accl, b), xa[b & 3]);
-          if (lane < G) xs[lane] = (xa[0] + xa[1]) + (xa[2] + xa[3]);
-        }
-      } else if (warp == 0) {
-        T cf[G];
-#pragma unroll
-        for (int b = 0; b < G; ++b) {
-          const int d = lane - b;
-          const bool on = d > 0 && d <= w && lane < G;
-          const T v = ROW(b)[on ? d : 0];  // in-bounds address either way
-          cf[b] = on ? v : T(0);
-        }
-        const int ml = lane < G ? lane : 0;
-        const T inv = rows[(size_t)(BWD ? G - 1 - ml : ml) * wp];
-        T acc = lane < G ? win[slot(lane)] : T(0);
-        T mine = T(0);
+        for (int b = 0; b < G; ++b) xa[b & 3] = fma(Di[b * G + ml], __shfl_sync(0xffffffffu, acc, b), xa[b & 3]);
+        x = (xa[0] + xa[1]) + (xa[2] + xa[3]);
+      } else {
+        const T inv = cur[(size_t)ml * wp];
 #pragma unroll
         for (int b = 0; b < G; ++b) {
           const T xb = __shfl_sync(0xffffffffu, acc * inv, b);
-          if (lane == b) mine = xb;
-          acc = fma(-cf[b], xb, acc);
+          if (lane == b) x = xb;
+          if (lane > b && lane < G) acc = fma(-cur[(size_t)b * wp + (lane - b)], xb, acc);
         }
-        if (lane < G) xs[lane] = mine;
       }
-      __syncthreads();
+      T* xc = xs + (st & 1) * 32;
+      if (lane < G) {
+        xc[lane] = x;
+        if (t0 + lane < S) xk[band(t0 + lane)] = x;
+      }
+      __syncwarp();
       T xr[G];
-      load_block<T, G>(xs, xr);
-      for (int e = tid; e < w; e += nth) {
-        const int i = t0 + G + e;
-        if (i < S) {
-          T acc[4] = {T(0), T(0), T(0), T(0)};  // four independent FMA chains
-          if (G + e <= w) {  // every row of the block reaches entry i
+      load_block<T, G>(xc, xr);
+      T cs[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-            for (int b = 0; b < G; ++b) acc[b & 3] = fma(ROW(b)[G + e - b], xr[b], acc[b & 3]);
+      for (int b = 0; b < G; ++b) cs[b & 3] = fma(cur[(size_t)b * wp + (G + ml - b)], xr[b], cs[b & 3]);
+      carry = (cs[0] + cs[1]) + (cs[2] + cs[3]);
+    } else {
+      if (st > 0) {
+        const T* prv = ring + (size_t)((st + kBandRing - 1) % kBandRing) * stage;
+        T xr[G];
+        load_block<T, G>(xs + ((st - 1) & 1) * 32, xr);
+        const int ne = min(w - G, Sp - t0 - G);
+        for (int e = wt; e < ne; e += wn) {
+          T acc[4] = {T(0), T(0), T(0), T(0)};  // four independent FMA chains
+          if (2 * G + e <= w) {                   // every row of block st-1 reaches entry t0+G+e
+#pragma unroll
+            for (int b = 0; b < G; ++b) acc[b & 3] = fma(prv[(size_t)b * wp + (2 * G + e - b)], xr[b], acc[b & 3]);
           } else {
 #pragma unroll
             for (int b = 0; b < G; ++b) {
-              const int d = G + e - b;
-              const T v = ROW(b)[d <= w ? d : 0];  // in-bounds address either way
+              const int d = 2 * G + e - b;
+              const T v = prv[(size_t)b * wp + (d <= w ? d : 0)];  // in-bounds address either way
               if (d <= w) acc[b & 3] = fma(v, xr[b], acc[b & 3]);
             }
           }
           win[slot(G + e)] -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
         }
       }
-#undef ROW
-    } else {
-      auto row = [&](int b) { return rows + (size_t)(band(t0 + b) - lo) * wp; };
-      if (warp == 0) {
-        T acc = lane < cnt ? win[slot(lane)] : T(0);
-        for (int b = 0; b < cnt; ++b) {
-          const T* f = row(b);
-          const T xb = __shfl_sync(0xffffffffu, acc, b) * f[0];
-          const int d = lane - b;
-          if (d > 0 && d <= w && lane < cnt) acc = fma(-f[d], xb, acc);
-          if (lane == b) xs[b] = xb;
-        }
-      }
-      __syncthreads();
-      for (int e = tid; e < w; e += nth) {
-        const int i = t0 + cnt + e;
-        if (i < S) {
-          T acc = T(0);
-          for (int b = 0; b < cnt; ++b) {
-            const int d = cnt + e - b;
-            if (d <= w) acc = fma(row(b)[d], xs[b], acc);  // d >= 1
-          }
-          win[slot(cnt + e)] -= acc;
-        }
-      }
-    }
-    if (tid < cnt) {
-      const int r = t0 + w + G + tid;
-      if (r < S) win[slot(tid)] = refill[(st % kBandRing) * G + tid];  // r = t0 + tid (mod W2)
-      xk[band(t0 + tid)] = xs[tid];
+      if (wt < G && t0 + w + wt < Sp) win[slot(w + wt)] = refill[(st % kBandRing) * G + wt];
     }
     s0 = slot(G);
   }
