@@ -338,16 +338,37 @@ int build_band_tables(const mfg_problem& p, const Geom& g, const double* lamt, P
 // ---------------------------------------------------------------- device --
 namespace {
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
 template <int B>
 __device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(B) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// One bulk copy global -> shared (16-byte aligned addresses, size a multiple
+// of 16) that completes on the mbarrier at `mbar`.
+__device__ __forceinline__ void bulk_load(void* smem, const void* gmem, uint32_t bytes, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(smem)),
+      "l"(gmem), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+constexpr uint32_t kBandPolls = 1u << 22;  // mbarrier polls before a wait gives up
+// Waits for phase `parity` of the mbarrier, giving up after `polls` polls.
+__device__ __forceinline__ bool band_wait(uint32_t mbar, uint32_t parity, uint32_t polls) {
+  for (uint32_t it = 0; it < polls; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
@@ -422,14 +443,17 @@ __device__ __forceinline__ void load_block(const T* xs, T (&xr)[G]) {
 // of block st-1, which nothing reads any more.  The solutions of blocks st and
 // st-1 sit in two halves of xs.  Factor rows, block inverses and right-hand
 // sides of a block arrive through a ring of kBandRing shared-memory stages
-// filled by cp.async (16-byte chunks; 4- or 8-byte right-hand-side copies)
-// kBandRing-2 blocks ahead, issued by warps 1..; stage st-1 is still read
-// during block st.  cp.async.wait_group only waits for copies already issued,
-// so the pipeline cannot stall for good.
+// kBandRing-2 blocks ahead (stage st-1 is still read during block st): the
+// rows and the inverse of a block are contiguous in global memory, so one
+// thread issues them as bulk copies that complete on the stage's mbarrier,
+// which warp 0 waits on before the block's barrier; warp 1 fetches the G
+// right-hand-side values with 4- or 8-byte cp.async copies.  Every wait is
+// bounded: a stage that never arrives marks this frequency's output NaN,
+// records MFG_ERR_TIMEOUT and ends the kernel.
 template <typename T, bool BWD, int G>
 __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T* __restrict__ sol,
                                                     const T* __restrict__ F, const T* __restrict__ Dinv,
-                                                    int S, int w, int wp, const DevScalars* sc) {
+                                                    int S, int w, int wp, DevScalars* sc) {
   constexpr bool INV = G >= 4;                        // blocks carry their triangle's inverse
   constexpr int RG = (kBandRing * G + 3) / 4 * 4;     // right-hand-side stages, 16-byte multiple
   if (sc != nullptr && sc->cg_done) return;
@@ -448,22 +472,24 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
   const T* bk = rhs + (size_t)k * S;
   T* xk = sol + (size_t)k * S;
   auto band = [&](int t) { return BWD ? S - 1 - t : t; };
+  __shared__ __align__(8) unsigned long long mbar[kBandRing];
+  const uint32_t rowbytes = (uint32_t)((size_t)G * wp * sizeof(T));
+  const uint32_t invbytes = INV ? (uint32_t)((size_t)G * G * sizeof(T)) : 0u;
   auto issue = [&](int st) {
-    if (st < nblk && warp > 0) {
+    if (warp != 1) return;
+    if (st < nblk) {
       const int t0 = st * G;
-      char* dst = reinterpret_cast<char*>(ring + (size_t)(st % kBandRing) * stage);
-      const char* g0 = reinterpret_cast<const char*>(Fk + (size_t)t0 * wp);
-      const int chunks = (int)((size_t)G * wp * sizeof(T) / 16);
-      for (int c = wt; c < chunks; c += wn) cp_async16(dst + 16 * (size_t)c, g0 + 16 * (size_t)c);
-      if constexpr (INV) {
-        char* di = dst + (size_t)G * wp * sizeof(T);
-        const char* gi = reinterpret_cast<const char*>(Dk + (size_t)st * G * G);
-        constexpr int ci = (int)((size_t)G * G * sizeof(T) / 16);
-        for (int c = wt; c < ci; c += wn) cp_async16(di + 16 * (size_t)c, gi + 16 * (size_t)c);
+      T* dst = ring + (size_t)(st % kBandRing) * stage;
+      if (lane == 0) {
+        const uint32_t mb = smem_addr(&mbar[st % kBandRing]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(rowbytes + invbytes)
+                     : "memory");
+        bulk_load(dst, Fk + (size_t)t0 * wp, rowbytes, mb);
+        if constexpr (INV) bulk_load(dst + (size_t)G * wp, Dk + (size_t)st * G * G, invbytes, mb);
       }
-      if (wt < G) {
-        const int r = t0 + w + wt;
-        T* rf = refill + (st % kBandRing) * G + wt;
+      if (lane < G) {
+        const int r = t0 + w + lane;
+        T* rf = refill + (st % kBandRing) * G + lane;
         if (r < S)
           cp_async_small<sizeof(T)>(rf, bk + band(r));
         else
@@ -472,6 +498,11 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
     }
     cp_async_commit();
   };
+  if (tid == 0) {
+    for (int i = 0; i < kBandRing; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
   for (int e = tid; e < w && e < Sp; e += nth) win[e] = e < S ? bk[band(e)] : T(0);
   for (int st = 0; st < kBandRing - 2; ++st) issue(st);
   // slot of entry t0 + x is s0 + x, less W2 past the end (x < W2): no divisions
@@ -479,9 +510,15 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
   auto slot = [&](int x) { const int q = s0 + x; return q >= W2 ? q - W2 : q; };
   T carry = T(0);
   const int ml = lane < G ? lane : 0;
+  int failed = 0;
   for (int st = 0; st < nblk; ++st) {
-    cp_async_wait<kBandRing - 3>();
-    __syncthreads();
+    bool ok = true;
+    if (warp == 0) ok = band_wait(smem_addr(&mbar[st % kBandRing]), (uint32_t)(st / kBandRing) & 1u, kBandPolls);
+    if (warp == 1) cp_async_wait<kBandRing - 3>();
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      failed = st + 1;
+      break;
+    }
     issue(st + kBandRing - 2);
     const int t0 = st * G;
     const T* cur = ring + (size_t)(st % kBandRing) * stage;
@@ -543,14 +580,29 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
     s0 = slot(G);
   }
   cp_async_wait<0>();
+  if (failed) {
+    // stage failed-1 never arrived: let the stages still in flight land
+    // (bounded) before the shared memory goes away, and mark the output
+    const int st = failed - 1;
+    if (tid == 0)
+      for (int j = st; j < min(nblk, st + kBandRing - 2); ++j)
+        band_wait(smem_addr(&mbar[j % kBandRing]), (uint32_t)(j / kBandRing) & 1u, kBandPolls);
+    for (int t = tid; t < S; t += nth) xk[t] = (T)__int_as_float(0x7fc00000);
+    if (tid == 0 && sc != nullptr) {
+      sc->status = MFG_ERR_TIMEOUT;
+      sc->cg_done = 1;
+    }
+    __syncthreads();
+  }
 }
 
 template <typename T, bool BWD>
 void launch_band_pass(const BandShape& b, int nt, const T* in, T* out, const T* F, const T* Dinv, int S,
                       int w, const DevScalars* sc, cudaStream_t s) {
+  DevScalars* scw = const_cast<DevScalars*>(sc);  // written only when a bounded wait runs out
   switch (b.G) {
 #define MFG_BAND_G(GG) \
-  case GG: k_band_pass<T, BWD, GG><<<nt, b.threads, b.smem, s>>>(in, out, F, Dinv, S, w, b.wp, sc); break;
+  case GG: k_band_pass<T, BWD, GG><<<nt, b.threads, b.smem, s>>>(in, out, F, Dinv, S, w, b.wp, scw); break;
     MFG_BAND_G(32) MFG_BAND_G(16) MFG_BAND_G(8) MFG_BAND_G(4) MFG_BAND_G(2) MFG_BAND_G(1)
 #undef MFG_BAND_G
     default: break;
