@@ -122,57 +122,66 @@ T* upload_vec(const std::vector<T>& h) {
   return d;
 }
 
-// padded row length: a multiple of 16 bytes so every row starts 16-byte aligned
-int band_row_words(int w, size_t elt) {
-  const int per16 = (int)(16 / elt);
-  return (w + 1 + per16 - 1) / per16 * per16;
-}
-
 // Launch shape of the substitutions.  G, the block of steps: the largest power
 // of two <= 32 with 2G <= w (the pipelined schedule below needs the next
-// block inside the band) whose stage (G factor rows, plus the G x G inverse of
-// the block's triangle when G >= 4) fits in kBandStageBytes.  The half-width
-// w is at least 2 (padded with zero coefficients), so G = 1 always fits.
+// block inside the band) whose stage fits in kBandStageBytes.  A block's stage
+// holds G (w + G) values, rounded up to 16 bytes: the G x G inverse of the
+// block's triangle, the G x G map from the block's right-hand side to its
+// contribution to the next block, and the coefficients of the w - G entries
+// after that.  The half-width w is at least 2 (padded with zero
+// coefficients), so G = 1 always fits.
 struct BandShape {
-  int wp, G, inv, stage, threads;
+  int G, stage, threads;
   size_t smem;
 };
 
 template <typename T>
 BandShape band_shape(int w) {
+  constexpr int V = 16 / (int)sizeof(T);
   BandShape b;
-  b.wp = band_row_words(w, sizeof(T));
-  auto stage = [&](int G) { return G * b.wp + (G >= 4 ? G * G : 0); };
+  auto stage = [&](int G) { return (G * (w + G) + V - 1) / V * V; };
   b.G = 1;
   while (b.G < 32 && 4 * b.G <= w && (size_t)stage(b.G * 2) * sizeof(T) <= (size_t)kBandStageBytes) b.G *= 2;
-  b.inv = b.G >= 4;
   b.stage = stage(b.G);
   // warp 0 solves the blocks; warps 1.. take the w - G far entries
   b.threads = std::min(512, std::max(64, 32 + (w - b.G + 31) / 32 * 32));
   const size_t rg = ((size_t)kBandRing * b.G + 3) / 4 * 4;
-  b.smem = sizeof(T) * ((size_t)kBandRing * b.stage + rg + 64 + (size_t)w + b.G);
+  b.smem = sizeof(T) * ((size_t)kBandRing * b.stage + rg + 96 + (size_t)w + b.G);
   return b;
 }
 
-// Factor rows in step order (the order the substitutions consume them),
-// padded to a whole number of blocks: step t of the forward solve L y = b is
-// band row t, with row (1/L_tt, L_{t+1,t}, ..., L_{t+w,t}); step t of the
-// backward solve L^T x = y is band row j = S-1-t, with row (1/L_jj, L_{j,j-1},
-// ..., L_{j,j-w}).  Entry d of a row couples step t to step t + d.  Padding
-// steps (t >= S) carry 1/L = 1 and no coupling.  For G >= 4 every block also
-// stores the transposed inverse of its G x G step-space triangle.
+// Position of entry c of row r in a stage section of G-wide rows.  When a row
+// is whole 16-byte chunks of V values (G a multiple of V), chunk q of row r
+// sits at chunk q ^ (r mod G/V): eight consecutive rows read at one chunk
+// index then fall in distinct banks.
+inline int band_pos(int r, int c, int G, int V) {
+  if (G % V != 0) return r * G + c;
+  const int nq = G / V;
+  return r * G + (((c / V) ^ (r & (nq - 1))) * V) + c % V;
+}
+
+// The substitution stages, in step order and padded to a whole number of
+// blocks.  Step t of the forward solve L y = b is band row t; step t of the
+// backward solve L^T x = y is band row S-1-t; coef(t, d) couples step t to
+// step t + d (L_{t+d,t} forward, L_{j,j-d} with j = S-1-t backward).  Padding
+// steps (t >= S) have a unit diagonal and no coupling.  For the block of steps
+// t0 .. t0+G-1 with step-space triangle T_blk (computed in FP64):
+//   rows l of section 0: row l of T_blk^{-1}           (x = T_blk^{-1} acc)
+//   rows l of section 1: row l of N T_blk^{-1}, with N[l][a] = coef(t0+a,
+//     G+l-a): the block's contribution to step t0+G+l, straight from acc
+//   rows e of section 2, e < w-G: coef(t0+b, 2G+e-b) at entry b, zero past
+//     the band: the block's contribution to step t0+2G+e.
 template <typename T>
 int build_factors(const Geom& g, const std::vector<Row>& chat, const std::vector<Row>& lhat,
                   const std::vector<int>& ipos, const double* lamt, int w, PrecTables* t,
                   std::string* err) {
   const int S = g.S, nt = g.nt;
+  constexpr int V = 16 / (int)sizeof(T);
   const BandShape bs = band_shape<T>(w);
-  const int G = bs.G, wp = bs.wp;
+  const int G = bs.G, stg = bs.stage;
   const int Sp = (S + G - 1) / G * G, nblk = Sp / G;
-  const size_t per = (size_t)Sp * wp;
-  const size_t perD = bs.inv ? (size_t)nblk * G * G : 0;
+  const size_t per = (size_t)nblk * stg;
   std::vector<T> Fc(per * nt, T(0)), Fr(per * nt, T(0));
-  std::vector<T> Dc(perD * nt, T(0)), Dr(perD * nt, T(0));
   std::vector<int> bad((size_t)nt, 0);
   auto work = [&](int k0, int k1) {
     std::vector<double> A((size_t)S * (w + 1));
@@ -195,43 +204,45 @@ int build_factors(const Geom& g, const std::vector<Row>& chat, const std::vector
         bad[(size_t)k] = 1;
         continue;
       }
-      // coupling of step tt to step tt + d in direction dir, 0 outside the matrix
-      auto coef = [&](int dir, int tt, int d) -> double {
-        if (tt >= S || tt + d >= S) return 0.0;
-        const int col = dir == 0 ? tt : S - 1 - tt - d;  // column of L in band storage
-        return A[(size_t)col * (w + 1) + d];
-      };
-      auto diag = [&](int dir, int tt) -> double {
-        if (tt >= S) return 1.0;
-        return A[(size_t)(dir == 0 ? tt : S - 1 - tt) * (w + 1)];
-      };
       for (int dir = 0; dir < 2; ++dir) {
+        // coupling of step tt to step tt + d (d <= w), 0 outside the matrix
+        auto coef = [&](int tt, int d) -> double {
+          if (tt >= S || tt + d >= S) return 0.0;
+          const int col = dir == 0 ? tt : S - 1 - tt - d;  // column of L in band storage
+          return A[(size_t)col * (w + 1) + d];
+        };
+        auto diag = [&](int tt) -> double {
+          if (tt >= S) return 1.0;
+          return A[(size_t)(dir == 0 ? tt : S - 1 - tt) * (w + 1)];
+        };
         T* F = (dir == 0 ? Fc.data() : Fr.data()) + per * k;
-        for (int tt = 0; tt < Sp; ++tt) {
-          F[(size_t)tt * wp] = (T)(1.0 / diag(dir, tt));
-          for (int d = 1; d <= w; ++d) F[(size_t)tt * wp + d] = (T)coef(dir, tt, d);
-        }
-        if (!bs.inv) continue;
-        // Step-space triangle of each block (steps t0 .. t0+G-1), inverted by
-        // forward substitution in FP64, stored transposed.
-        T* D = (dir == 0 ? Dc.data() : Dr.data()) + perD * k;
         for (int blk = 0; blk < nblk; ++blk) {
           const int t0 = blk * G;
+          T* B = F + (size_t)blk * stg;
           std::fill(Tm.begin(), Tm.end(), 0.0);
           for (int a = 0; a < G; ++a) {
-            Tm[(size_t)a * G + a] = diag(dir, t0 + a);
-            for (int b = 0; b < a; ++b)
-              if (a - b <= w) Tm[(size_t)a * G + b] = coef(dir, t0 + b, a - b);
+            Tm[(size_t)a * G + a] = diag(t0 + a);
+            for (int c = 0; c < a; ++c) Tm[(size_t)a * G + c] = coef(t0 + c, a - c);  // a - c < G <= w
           }
+          // inverse of the lower triangle by forward substitution, column by column
           for (int c = 0; c < G; ++c)
             for (int a = 0; a < G; ++a) {
               double v = (a == c) ? 1.0 : 0.0;
-              for (int b = c; b < a; ++b) v -= Tm[(size_t)a * G + b] * Ti[(size_t)b * G + c];
+              for (int m = c; m < a; ++m) v -= Tm[(size_t)a * G + m] * Ti[(size_t)m * G + c];
               Ti[(size_t)a * G + c] = (a >= c) ? v / Tm[(size_t)a * G + a] : 0.0;
             }
-          T* Db = D + (size_t)blk * G * G;
-          for (int a = 0; a < G; ++a)
-            for (int b = 0; b < G; ++b) Db[(size_t)b * G + a] = (T)Ti[(size_t)a * G + b];
+          for (int l = 0; l < G; ++l)
+            for (int c = 0; c < G; ++c) {
+              B[band_pos(l, c, G, V)] = (T)Ti[(size_t)l * G + c];
+              double m = 0.0;  // (N T^{-1})[l][c], T^{-1} lower triangular
+              for (int a = c; a < G; ++a) m += coef(t0 + a, G + l - a) * Ti[(size_t)a * G + c];
+              B[(size_t)G * G + band_pos(l, c, G, V)] = (T)m;
+            }
+          for (int e = 0; e < w - G; ++e)
+            for (int c = 0; c < G; ++c) {
+              const int d = 2 * G + e - c;
+              B[(size_t)2 * G * G + band_pos(e, c, G, V)] = d <= w ? (T)coef(t0 + c, d) : T(0);
+            }
         }
       }
     }
@@ -247,20 +258,14 @@ int build_factors(const Geom& g, const std::vector<Row>& chat, const std::vector
     }
   T* dc = upload_vec(Fc);
   T* dr = upload_vec(Fr);
-  T* ic = bs.inv ? upload_vec(Dc) : nullptr;
-  T* ir = bs.inv ? upload_vec(Dr) : nullptr;
   if constexpr (sizeof(T) == 8) {
     t->bandc64 = dc;
     t->bandr64 = dr;
-    t->bandic64 = ic;
-    t->bandir64 = ir;
   } else {
     t->bandc32 = dc;
     t->bandr32 = dr;
-    t->bandic32 = ic;
-    t->bandir32 = ir;
   }
-  if (!dc || !dr || (bs.inv && (!ic || !ir))) {
+  if (!dc || !dr) {
     *err = "cudaMalloc failed for the banded factors";
     return MFG_ERR_CUDA;  // the caller frees what was uploaded
   }
@@ -317,7 +322,7 @@ int build_band_tables(const mfg_problem& p, const Geom& g, const double* lamt, P
   }
   w = std::max(w, 2);  // the pipelined substitutions need 2G <= w with G >= 1
   const size_t elt = p.precision == MFG_FP64 ? 8 : 4;
-  const double bytes = 2.0 * g.nt * (double)S * band_row_words(w, elt) * elt;
+  const double bytes = 2.0 * g.nt * ((double)S + 32) * (w + 32) * elt;  // stages: G (w + G) per G steps
   if (w > kBandMaxW || bytes > kBandMaxBytes) {
     *err = "viscosity field: banded factors too large (half-bandwidth " + std::to_string(w) +
            ", " + std::to_string(bytes / 1073741824.0) + " GiB)";
@@ -422,70 +427,92 @@ __device__ __forceinline__ void load_block(const T* xs, T (&xr)[G]) {
   }
 }
 
+// Dot product of row r of a stage section (G-wide rows, layout band_pos)
+// with xr: 16-byte loads when rows are whole chunks, four FMA chains.
+template <typename T, int G>
+__device__ __forceinline__ T row_dot(const T* sec, int r, const T (&xr)[G]) {
+  constexpr int V = 16 / (int)sizeof(T);
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  const T* row = sec + r * G;
+  if constexpr (G % V == 0) {
+    constexpr int NQ = G / V;
+    const int sw = r & (NQ - 1);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const T* p = row + ((q ^ sw) * V);
+      if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        acc[0] = fma(v.x, xr[4 * q], acc[0]);
+        acc[1] = fma(v.y, xr[4 * q + 1], acc[1]);
+        acc[2] = fma(v.z, xr[4 * q + 2], acc[2]);
+        acc[3] = fma(v.w, xr[4 * q + 3], acc[3]);
+      } else {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        acc[(2 * q) & 3] = fma(v.x, xr[2 * q], acc[(2 * q) & 3]);
+        acc[(2 * q + 1) & 3] = fma(v.y, xr[2 * q + 1], acc[(2 * q + 1) & 3]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < G; ++c) acc[c & 3] = fma(row[c], xr[c], acc[c & 3]);
+  }
+  return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
 // One banded substitution per frequency (blockIdx.x = k).  Both directions are
 // the same lower-triangular banded solve in step order t = 0..S'-1 (S' = S
-// rounded up to whole blocks; padding steps have a unit diagonal, no coupling
-// and a zero right-hand side): row t of F holds 1/L_tt and the coefficients
-// coupling step t to steps t+1 .. t+w (forward: band row t of L; backward:
-// band row S-1-t of L^T).  Steps go in blocks of G (a power of two <= 32,
-// 2G <= w) with a one-block lag between the two kinds of work:
-//   warp 0 solves block st: its right-hand side is the window entry less
-//     `carry`, the contribution of block st-1 that warp 0 computed itself; the
-//     G x G triangle is one product with its inverse for G >= 4 (formed on the
-//     host in FP64 and streamed with the rows; lane a sums G terms, no
-//     dependency chain), else a shuffle chain; then it forms block st's
-//     contribution to block st+1 (distances G+l-b <= 2G-1 <= w) in `carry`;
+// rounded up to whole blocks of G steps; G a power of two <= 32 with
+// 2G <= w), with a one-block lag between the two kinds of work:
+//   warp 0 solves block st.  Its right-hand side acc is the window entries
+//     less `carry` (block st-1's contribution, which warp 0 formed itself);
+//     every lane reads all of acc and forms, as two G-term dot products with
+//     rows of the block's stage, x = T^{-1} acc and its next `carry`
+//     = N T^{-1} acc (the host formed both matrices in FP64);
 //   warps 1.. meanwhile subtract block st-1's contribution from entries
-//     t0+G .. t0+w-1 (distance 2G+e-b, zero past w) and copy the right-hand
-//     side of entries t0+w .. t0+w+G-1 into the window.
+//     t0+G .. t0+w-1 (thread e: one G-term dot product with row e of the far
+//     section, zeros past the band) and copy the right-hand side of entries
+//     t0+w .. t0+w+G-1 into the window.
 // One barrier per block.  The window keeps entry t at slot t mod (w+G): during
 // block st it holds entries t0 .. t0+w+G-1, the new entries taking the slots
 // of block st-1, which nothing reads any more.  The solutions of blocks st and
-// st-1 sit in two halves of xs.  Factor rows, block inverses and right-hand
-// sides of a block arrive through a ring of kBandRing shared-memory stages
-// kBandRing-2 blocks ahead (stage st-1 is still read during block st): the
-// rows and the inverse of a block are contiguous in global memory, so one
-// thread issues them as bulk copies that complete on the stage's mbarrier,
+// st-1 sit in two halves of xs.  Each block's stage is contiguous in global
+// memory and arrives through a ring of kBandRing shared-memory stages
+// kBandRing-2 blocks ahead (stage st-1 is still read during block st): one
+// thread issues it as a bulk copy that completes on the stage's mbarrier,
 // which warp 0 waits on before the block's barrier; warp 1 fetches the G
 // right-hand-side values with 4- or 8-byte cp.async copies.  Every wait is
 // bounded: a stage that never arrives marks this frequency's output NaN,
 // records MFG_ERR_TIMEOUT and ends the kernel.
 template <typename T, bool BWD, int G>
 __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T* __restrict__ sol,
-                                                    const T* __restrict__ F, const T* __restrict__ Dinv,
-                                                    int S, int w, int wp, DevScalars* sc) {
-  constexpr bool INV = G >= 4;                        // blocks carry their triangle's inverse
+                                                    const T* __restrict__ F, int S, int w, int stage,
+                                                    DevScalars* sc) {
   constexpr int RG = (kBandRing * G + 3) / 4 * 4;     // right-hand-side stages, 16-byte multiple
   if (sc != nullptr && sc->cg_done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int stage = G * wp + (INV ? G * G : 0);
-  T* ring = reinterpret_cast<T*>(smraw);              // kBandRing x (G rows of wp [+ G x G inverse])
+  T* ring = reinterpret_cast<T*>(smraw);              // kBandRing stages
   T* refill = ring + (size_t)kBandRing * stage;       // kBandRing x G
   T* xs = refill + RG;                                // 2 x 32
-  T* win = xs + 64;                                   // w + G
+  T* accb = xs + 64;                                  // 32: the block's right-hand side
+  T* win = accb + 32;                                 // w + G
   const int k = blockIdx.x, tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int wt = tid - 32, wn = nth - 32;             // rank among warps 1..
   const int W2 = w + G;
   const int Sp = (S + G - 1) / G * G, nblk = Sp / G;
-  const T* Fk = F + (size_t)k * Sp * wp;
-  const T* Dk = INV ? Dinv + (size_t)k * nblk * G * G : nullptr;
+  const T* Fk = F + (size_t)k * nblk * stage;
   const T* bk = rhs + (size_t)k * S;
   T* xk = sol + (size_t)k * S;
   auto band = [&](int t) { return BWD ? S - 1 - t : t; };
   __shared__ __align__(8) unsigned long long mbar[kBandRing];
-  const uint32_t rowbytes = (uint32_t)((size_t)G * wp * sizeof(T));
-  const uint32_t invbytes = INV ? (uint32_t)((size_t)G * G * sizeof(T)) : 0u;
+  const uint32_t sbytes = (uint32_t)((size_t)stage * sizeof(T));
   auto issue = [&](int st) {
     if (warp != 1) return;
     if (st < nblk) {
       const int t0 = st * G;
-      T* dst = ring + (size_t)(st % kBandRing) * stage;
       if (lane == 0) {
         const uint32_t mb = smem_addr(&mbar[st % kBandRing]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(rowbytes + invbytes)
-                     : "memory");
-        bulk_load(dst, Fk + (size_t)t0 * wp, rowbytes, mb);
-        if constexpr (INV) bulk_load(dst + (size_t)G * wp, Dk + (size_t)st * G * G, invbytes, mb);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(sbytes) : "memory");
+        bulk_load(ring + (size_t)(st % kBandRing) * stage, Fk + (size_t)st * stage, sbytes, mb);
       }
       if (lane < G) {
         const int r = t0 + w + lane;
@@ -521,59 +548,26 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
     }
     issue(st + kBandRing - 2);
     const int t0 = st * G;
-    const T* cur = ring + (size_t)(st % kBandRing) * stage;
     if (warp == 0) {
-      T acc = lane < G ? win[slot(lane)] - carry : T(0);
-      T x = T(0);
-      if constexpr (INV) {
-        // x = T^{-1} acc with the block's inverse (transposed in the stage)
-        const T* Di = cur + (size_t)G * wp;
-        T xa[4] = {T(0), T(0), T(0), T(0)};  // four independent FMA chains
-#pragma unroll
-        for (int b = 0; b < G; ++b) xa[b & 3] = fma(Di[b * G + ml], __shfl_sync(0xffffffffu, acc, b), xa[b & 3]);
-        x = (xa[0] + xa[1]) + (xa[2] + xa[3]);
-      } else {
-        const T inv = cur[(size_t)ml * wp];
-#pragma unroll
-        for (int b = 0; b < G; ++b) {
-          const T xb = __shfl_sync(0xffffffffu, acc * inv, b);
-          if (lane == b) x = xb;
-          if (lane > b && lane < G) acc = fma(-cur[(size_t)b * wp + (lane - b)], xb, acc);
-        }
-      }
+      const T* cur = ring + (size_t)(st % kBandRing) * stage;
+      if (lane < G) accb[lane] = win[slot(lane)] - carry;
+      __syncwarp();
+      T ar[G];
+      load_block<T, G>(accb, ar);
+      const T x = row_dot<T, G>(cur, ml, ar);
+      carry = row_dot<T, G>(cur + G * G, ml, ar);
       T* xc = xs + (st & 1) * 32;
       if (lane < G) {
         xc[lane] = x;
         if (t0 + lane < S) xk[band(t0 + lane)] = x;
       }
-      __syncwarp();
-      T xr[G];
-      load_block<T, G>(xc, xr);
-      T cs[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-      for (int b = 0; b < G; ++b) cs[b & 3] = fma(cur[(size_t)b * wp + (G + ml - b)], xr[b], cs[b & 3]);
-      carry = (cs[0] + cs[1]) + (cs[2] + cs[3]);
     } else {
       if (st > 0) {
-        const T* prv = ring + (size_t)((st + kBandRing - 1) % kBandRing) * stage;
+        const T* far = ring + (size_t)((st + kBandRing - 1) % kBandRing) * stage + 2 * G * G;
         T xr[G];
         load_block<T, G>(xs + ((st - 1) & 1) * 32, xr);
         const int ne = min(w - G, Sp - t0 - G);
-        for (int e = wt; e < ne; e += wn) {
-          T acc[4] = {T(0), T(0), T(0), T(0)};  // four independent FMA chains
-          if (2 * G + e <= w) {                   // every row of block st-1 reaches entry t0+G+e
-#pragma unroll
-            for (int b = 0; b < G; ++b) acc[b & 3] = fma(prv[(size_t)b * wp + (2 * G + e - b)], xr[b], acc[b & 3]);
-          } else {
-#pragma unroll
-            for (int b = 0; b < G; ++b) {
-              const int d = 2 * G + e - b;
-              const T v = prv[(size_t)b * wp + (d <= w ? d : 0)];  // in-bounds address either way
-              if (d <= w) acc[b & 3] = fma(v, xr[b], acc[b & 3]);
-            }
-          }
-          win[slot(G + e)] -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
-        }
+        for (int e = wt; e < ne; e += wn) win[slot(G + e)] -= row_dot<T, G>(far, e, xr);
       }
       if (wt < G && t0 + w + wt < Sp) win[slot(w + wt)] = refill[(st % kBandRing) * G + wt];
     }
@@ -597,12 +591,12 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
 }
 
 template <typename T, bool BWD>
-void launch_band_pass(const BandShape& b, int nt, const T* in, T* out, const T* F, const T* Dinv, int S,
-                      int w, const DevScalars* sc, cudaStream_t s) {
+void launch_band_pass(const BandShape& b, int nt, const T* in, T* out, const T* F, int S, int w,
+                      const DevScalars* sc, cudaStream_t s) {
   DevScalars* scw = const_cast<DevScalars*>(sc);  // written only when a bounded wait runs out
   switch (b.G) {
 #define MFG_BAND_G(GG) \
-  case GG: k_band_pass<T, BWD, GG><<<nt, b.threads, b.smem, s>>>(in, out, F, Dinv, S, w, b.wp, scw); break;
+  case GG: k_band_pass<T, BWD, GG><<<nt, b.threads, b.smem, s>>>(in, out, F, S, w, b.stage, scw); break;
     MFG_BAND_G(32) MFG_BAND_G(16) MFG_BAND_G(8) MFG_BAND_G(4) MFG_BAND_G(2) MFG_BAND_G(1)
 #undef MFG_BAND_G
     default: break;
@@ -610,16 +604,15 @@ void launch_band_pass(const BandShape& b, int nt, const T* in, T* out, const T* 
 }
 
 template <typename T>
-void precond_band_typed(const Geom& g, const PrecTables& t, const T* V, const T* Lc, const T* Lr,
-                        const T* Ic, const T* Ir, const double* r, double* z, T* w0, T* w1,
-                        const DevScalars* sc, cudaStream_t s) {
+void precond_band_typed(const Geom& g, const PrecTables& t, const T* V, const T* Fc, const T* Fr,
+                        const double* r, double* z, T* w0, T* w1, const DevScalars* sc, cudaStream_t s) {
   const int S = g.S, nt = g.nt, w = t.band_w;
   const size_t tsm = sizeof(T) * (size_t)nt * 32;
   const int tb = (S + 31) / 32;
   k_time_xf<double, T, T, false, true><<<tb, 256, tsm, s>>>(r, w0, V, t.band_perm, nt, S, sc);
   const BandShape b = band_shape<T>(w);
-  launch_band_pass<T, false>(b, nt, w0, w1, Lc, Ic, S, w, sc, s);
-  launch_band_pass<T, true>(b, nt, w1, w0, Lr, Ir, S, w, sc, s);
+  launch_band_pass<T, false>(b, nt, w0, w1, Fc, S, w, sc, s);
+  launch_band_pass<T, true>(b, nt, w1, w0, Fr, S, w, sc, s);
   k_time_xf<T, double, T, true, false><<<tb, 256, tsm, s>>>(w0, z, V, t.band_perm, nt, S, sc);
 }
 
@@ -659,11 +652,9 @@ int band_configure() {
 void launch_precond_band(const Geom& g, const PrecTables& t, int precision, const double* r, double* z,
                          double* work64, float* work32, const DevScalars* sc, cudaStream_t s) {
   if (precision == MFG_FP64)
-    precond_band_typed<double>(g, t, t.Vt64, t.bandc64, t.bandr64, t.bandic64, t.bandir64, r, z, work64,
-                               work64 + g.n, sc, s);
+    precond_band_typed<double>(g, t, t.Vt64, t.bandc64, t.bandr64, r, z, work64, work64 + g.n, sc, s);
   else
-    precond_band_typed<float>(g, t, t.Vt32, t.bandc32, t.bandr32, t.bandic32, t.bandir32, r, z, work32,
-                              work32 + g.n, sc, s);
+    precond_band_typed<float>(g, t, t.Vt32, t.bandc32, t.bandr32, r, z, work32, work32 + g.n, sc, s);
 }
 
 }  // namespace mfg

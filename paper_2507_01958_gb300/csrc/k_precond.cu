@@ -217,8 +217,7 @@ void free_prec_tables(PrecTables* t) {
                   t->Vt32, t->lamt32, t->L1_32, t->L2_32, t->twx64, t->twx32, t->dctx64, t->dctx32,
                   t->twy64, t->twy32, t->dcty64, t->dcty32, t->thc64, t->thd64, t->tho64,
                   t->thc32, t->thd32, t->tho32, t->kfx, t->kfy, t->band_perm, t->bandc64,
-                  t->bandr64, t->bandc32, t->bandr32, t->bandic64, t->bandir64, t->bandic32,
-                  t->bandir32};
+                  t->bandr64, t->bandc32, t->bandr32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   *t = PrecTables{};

@@ -134,17 +134,12 @@ struct PrecTables {
   double *kfx = nullptr, *kfy = nullptr;
   int band_w = 0;                 // half-bandwidth w of the factors
   int* band_perm = nullptr;       // band position -> plane index (S ints)
-  // Factor of frequency k in two layouts of S (w+1) words each, at offset
-  // k S (w+1): by columns (Lc[j(w+1)] = 1/L_jj, Lc[j(w+1)+1+e] = L_{j+1+e, j})
-  // and by rows (Lr[j(w+1)] = 1/L_jj, Lr[j(w+1)+1+e] = L_{j, j-1-e}); zero
-  // outside the matrix.  One precision is allocated: FP64 for MFG_FP64, FP32
-  // otherwise.
+  // Substitution stages of frequency k, forward (c) and backward (r): one
+  // stage of G (w + G) values (rounded up to 16 bytes) per block of G steps,
+  // at offset k nblk stage (layout in k_band.cu).  One precision is
+  // allocated: FP64 for MFG_FP64, FP32 otherwise.
   double *bandc64 = nullptr, *bandr64 = nullptr;
   float *bandc32 = nullptr, *bandr32 = nullptr;
-  // Inverses of the G x G step-space triangles of the full blocks of the
-  // substitutions (forward: c, backward: r; null when G < 4), transposed.
-  double *bandic64 = nullptr, *bandir64 = nullptr;
-  float *bandic32 = nullptr, *bandir32 = nullptr;
 };
 // Tensor-core time pass (MFG_MIXED_TC), for N_t in {32, 64, 128}.
 bool time_tc_supported(int nt);
