@@ -143,10 +143,11 @@ BandShape band_shape(int w) {
   b.G = 1;
   while (b.G < 32 && 4 * b.G <= w && (size_t)stage(b.G * 2) * sizeof(T) <= (size_t)kBandStageBytes) b.G *= 2;
   b.stage = stage(b.G);
-  // warp 0 solves the blocks; warps 1.. take the w - G far entries
-  b.threads = std::min(512, std::max(64, 32 + (w - b.G + 31) / 32 * 32));
+  // warps 0 and 1 solve the blocks, warp 2 moves the data, warps 3.. take
+  // the w - G far entries
+  b.threads = std::min(512, 96 + (w - b.G + 31) / 32 * 32);
   const size_t rg = ((size_t)kBandRing * b.G + 3) / 4 * 4;
-  b.smem = sizeof(T) * ((size_t)kBandRing * b.stage + rg + 96 + (size_t)w + b.G);
+  b.smem = sizeof(T) * ((size_t)kBandRing * b.stage + rg + 192 + (size_t)w + b.G);
   return b;
 }
 
@@ -462,16 +463,18 @@ __device__ __forceinline__ T row_dot(const T* sec, int r, const T (&xr)[G]) {
 // One banded substitution per frequency (blockIdx.x = k).  Both directions are
 // the same lower-triangular banded solve in step order t = 0..S'-1 (S' = S
 // rounded up to whole blocks of G steps; G a power of two <= 32 with
-// 2G <= w), with a one-block lag between the two kinds of work:
-//   warp 0 solves block st.  Its right-hand side acc is the window entries
-//     less `carry` (block st-1's contribution, which warp 0 formed itself);
-//     every lane reads all of acc and forms, as two G-term dot products with
-//     rows of the block's stage, x = T^{-1} acc and its next `carry`
-//     = N T^{-1} acc (the host formed both matrices in FP64);
-//   warps 1.. meanwhile subtract block st-1's contribution from entries
-//     t0+G .. t0+w-1 (thread e: one G-term dot product with row e of the far
-//     section, zeros past the band) and copy the right-hand side of entries
-//     t0+w .. t0+w+G-1 into the window.
+// 2G <= w), with a one-block lag between the kinds of work:
+//   warps 0 and 1 solve block st.  Its right-hand side acc is the window
+//     entries less `carry`, block st-1's contribution to them, which warp 1
+//     formed in the previous block.  Both warps read all of acc; lane l of
+//     warp 0 forms x_l = (T^{-1} acc)_l and lane l of warp 1 the next carry
+//     (N T^{-1} acc)_l, each a G-term dot product with a row of the block's
+//     stage (the host formed both matrices in FP64);
+//   warp 2 issues the copies of block st+kBandRing-2 and moves the right-hand
+//     side of entries t0+w .. t0+w+G-1 into the window;
+//   warps 3.. subtract block st-1's contribution from entries t0+G .. t0+w-1
+//     (thread e: one G-term dot product with row e of the far section, zeros
+//     past the band).
 // One barrier per block.  The window keeps entry t at slot t mod (w+G): during
 // block st it holds entries t0 .. t0+w+G-1, the new entries taking the slots
 // of block st-1, which nothing reads any more.  The solutions of blocks st and
@@ -479,7 +482,7 @@ __device__ __forceinline__ T row_dot(const T* sec, int r, const T (&xr)[G]) {
 // memory and arrives through a ring of kBandRing shared-memory stages
 // kBandRing-2 blocks ahead (stage st-1 is still read during block st): one
 // thread issues it as a bulk copy that completes on the stage's mbarrier,
-// which warp 0 waits on before the block's barrier; warp 1 fetches the G
+// which warp 0 waits on before the block's barrier; warp 2 fetches the G
 // right-hand-side values with 4- or 8-byte cp.async copies.  Every wait is
 // bounded: a stage that never arrives marks this frequency's output NaN,
 // records MFG_ERR_TIMEOUT and ends the kernel.
@@ -493,10 +496,11 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
   T* ring = reinterpret_cast<T*>(smraw);              // kBandRing stages
   T* refill = ring + (size_t)kBandRing * stage;       // kBandRing x G
   T* xs = refill + RG;                                // 2 x 32
-  T* accb = xs + 64;                                  // 32: the block's right-hand side
-  T* win = accb + 32;                                 // w + G
+  T* accb = xs + 64;                                  // 2 x 32: the block's right-hand side (warps 0, 1)
+  T* cb = accb + 64;                                  // 2 x 32: carry of the current and previous block
+  T* win = cb + 64;                                   // w + G
   const int k = blockIdx.x, tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  const int wt = tid - 32, wn = nth - 32;             // rank among warps 1..
+  const int wt = tid - 96, wn = nth - 96;             // rank among warps 3..
   const int W2 = w + G;
   const int Sp = (S + G - 1) / G * G, nblk = Sp / G;
   const T* Fk = F + (size_t)k * nblk * stage;
@@ -506,7 +510,7 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
   __shared__ __align__(8) unsigned long long mbar[kBandRing];
   const uint32_t sbytes = (uint32_t)((size_t)stage * sizeof(T));
   auto issue = [&](int st) {
-    if (warp != 1) return;
+    if (warp != 2) return;
     if (st < nblk) {
       const int t0 = st * G;
       if (lane == 0) {
@@ -529,38 +533,44 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
     for (int i = 0; i < kBandRing; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (tid < 64) cb[tid] = T(0);
   __syncthreads();
   for (int e = tid; e < w && e < Sp; e += nth) win[e] = e < S ? bk[band(e)] : T(0);
   for (int st = 0; st < kBandRing - 2; ++st) issue(st);
   // slot of entry t0 + x is s0 + x, less W2 past the end (x < W2): no divisions
   int s0 = 0;
   auto slot = [&](int x) { const int q = s0 + x; return q >= W2 ? q - W2 : q; };
-  T carry = T(0);
   const int ml = lane < G ? lane : 0;
   int failed = 0;
   for (int st = 0; st < nblk; ++st) {
     bool ok = true;
     if (warp == 0) ok = band_wait(smem_addr(&mbar[st % kBandRing]), (uint32_t)(st / kBandRing) & 1u, kBandPolls);
-    if (warp == 1) cp_async_wait<kBandRing - 3>();
+    if (warp == 2) cp_async_wait<kBandRing - 3>();
     if (__syncthreads_or(ok ? 0 : 1)) {
       failed = st + 1;
       break;
     }
     issue(st + kBandRing - 2);
     const int t0 = st * G;
-    if (warp == 0) {
+    if (warp < 2) {
       const T* cur = ring + (size_t)(st % kBandRing) * stage;
-      if (lane < G) accb[lane] = win[slot(lane)] - carry;
+      T* ab = accb + warp * 32;
+      if (lane < G) ab[lane] = win[slot(lane)] - cb[((st + 1) & 1) * 32 + lane];
       __syncwarp();
       T ar[G];
-      load_block<T, G>(accb, ar);
-      const T x = row_dot<T, G>(cur, ml, ar);
-      carry = row_dot<T, G>(cur + G * G, ml, ar);
-      T* xc = xs + (st & 1) * 32;
-      if (lane < G) {
-        xc[lane] = x;
-        if (t0 + lane < S) xk[band(t0 + lane)] = x;
+      load_block<T, G>(ab, ar);
+      if (warp == 0) {
+        const T x = row_dot<T, G>(cur, ml, ar);
+        if (lane < G) {
+          xs[(st & 1) * 32 + lane] = x;
+          if (t0 + lane < S) xk[band(t0 + lane)] = x;
+        }
+      } else {
+        const T c = row_dot<T, G>(cur + G * G, ml, ar);
+        if (lane < G) cb[(st & 1) * 32 + lane] = c;
       }
+    } else if (warp == 2) {
+      if (lane < G && t0 + w + lane < Sp) win[slot(w + lane)] = refill[(st % kBandRing) * G + lane];
     } else {
       if (st > 0) {
         const T* far = ring + (size_t)((st + kBandRing - 1) % kBandRing) * stage + 2 * G * G;
@@ -569,7 +579,6 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
         const int ne = min(w - G, Sp - t0 - G);
         for (int e = wt; e < ne; e += wn) win[slot(G + e)] -= row_dot<T, G>(far, e, xr);
       }
-      if (wt < G && t0 + w + wt < Sp) win[slot(w + wt)] = refill[(st % kBandRing) * G + wt];
     }
     s0 = slot(G);
   }
