@@ -127,7 +127,7 @@ typedef struct {
  * device in the plan's preconditioner precision (FP32 for the MIXED
  * precisions), and applied per frequency by forward and backward banded
  * substitution between the two time transforms.  Costs: factor storage
- * 2 N_t Nx Ny (w+1) words, w the half-bandwidth (2 Ny on a Neumann x axis,
+ * about 2 N_t Nx Ny (w+32) words, w the half-bandwidth (2 Ny on a Neumann x axis,
  * ~4 Ny + Ny on a periodic one), and O(N_t Nx Ny w^2) host work in mfg_plan.
  * Restrictions: l must be 1 or 2 (MFG_ERR_UNSUPPORTED for l = 0); w <= 4096
  * and factor storage <= 64 GiB (MFG_ERR_UNSUPPORTED beyond);

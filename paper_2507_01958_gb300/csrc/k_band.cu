@@ -15,11 +15,13 @@
 //   time forward (scatter to band order) -> L y = b -> L^T x = y -> time
 //   inverse (gather from band order).
 // The substitutions are sequential along the band: one CTA per frequency
-// walks its S points in blocks of up to 32 (a warp-shuffle triangular solve,
-// then a block update of the next w partial sums, held in a circular window
-// in shared memory); the factor rows, contiguous in memory in the order they
-// are used, stream through a ring of shared-memory stages filled by cp.async
-// several blocks ahead, so the loads never wait on the dependency chain.
+// walks its S points in blocks of up to 32 steps.  Two warps solve a block
+// (its inverted triangle and its map to the next block, both formed on the
+// host), the other warps apply the previous block to the later partial sums
+// (a circular window in shared memory), one block behind; each block's
+// coefficients are one contiguous stage that a bulk copy brings into a ring
+// of shared-memory stages a few blocks ahead, so the loads never wait on the
+// dependency chain.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -32,7 +34,7 @@ namespace mfg {
 
 namespace {
 
-constexpr int kBandRing = 5;           // shared-memory stages of factor rows
+constexpr int kBandRing = 5;           // shared-memory stages of the substitutions
 constexpr int kBandStageBytes = 40 * 1024;
 constexpr int kBandMaxW = 4096;
 constexpr double kBandMaxBytes = 64.0 * 1024 * 1024 * 1024;

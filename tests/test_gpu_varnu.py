@@ -121,6 +121,47 @@ def test_field_precond_fp32_backward_error(case, precision):
     assert eta <= bar
 
 
+# Shapes of the substitutions' block schedule (the block size G follows from
+# the half-bandwidth w: the largest power of two <= 32 with 2G <= w whose
+# stage fits the kernel's budget): G = 32 with a partial last block (7 x 33 Neumann, w = 66,
+# S = 231), G = 32 with three blocks (5 x 17, periodic x, w = 68, S = 85),
+# fewer blocks than copies in flight (1-D with two points; 2 x 2 periodic),
+# and G = 2 with three blocks (3 x 2 periodic, w = 5).
+BAND_SHAPES = [
+    (71, 2, 7, 33, 4, ("neumann", "neumann"), "smooth", 10.0, 1),
+    (72, 2, 5, 17, 5, ("periodic", "neumann"), "layers", 10.0, 1),
+    (73, 1, 2, 1, 4, ("periodic", "periodic"), "smooth", 5.0, 1),
+    (74, 2, 2, 2, 3, ("periodic", "periodic"), "smooth", 5.0, 2),
+    (75, 2, 3, 2, 6, ("periodic", "periodic"), "layers", 8.0, 1),
+]
+
+
+@pytest.mark.parametrize("case", BAND_SHAPES)
+def test_field_precond_band_shapes(case):
+    """P^{-1} r on the block-schedule shapes above: FP64 against Alg. 1 with
+    sparse LU (forward error, as in the FP64 test), FP32 by its normwise
+    backward error (the bar of the FP32 test)."""
+    import torch
+    inst = _inst(case)
+    p = inst["problem"]
+    L = lib()
+    n = ops.sizes(p)[1]
+    r = mi.random_field(n, 9)
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    L.mfg_apply_precond(_plan(p, "fp64"), 0, dev(r), z)
+    err = rel(host(z), solvers.precond_lu(p, r))
+    L.mfg_apply_precond(_plan(p, "mixed_tc"), 0, dev(r), z)
+    P = ops.precond(p)
+    zh = host(z)
+    eta = np.linalg.norm(r - P @ zh) / (abs(P).sum(axis=0).max() * np.linalg.norm(zh) + np.linalg.norm(r))
+    nx, ny = p["n"]
+    w = 4 * ny + ny if p["dim"] == 2 else 4
+    bar = (3 * w + 3 + 2 * p["nt"]) * 2.0 ** -24
+    print(f"\nband shape {case[2]}x{case[3]}: FP64 rel err {err:.2e}, FP32 backward error {eta:.2e} (bar {bar:.1e})")
+    assert err <= 1e-8
+    assert eta <= bar
+
+
 def _field_cond(p):
     """cond(AAt) by dense eigenvalues (the small grids of this file)."""
     ev = np.linalg.eigvalsh(ops.AAt(p).toarray())
