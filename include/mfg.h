@@ -312,9 +312,13 @@ int mfg_get_schedule(mfg_plan_t plan, int b, mfg_schedule* out);
  * and the bounded mbarrier wait (4096 polls under this hook) runs out: the
  * instance ends with MFG_ERR_TIMEOUT after its first CP iteration (outputs
  * unspecified, as for any timeout) and the call returns normally with the
- * context still usable.  Applies to the plan's later mfg_solve calls (no
- * graph rebuild).  Invalid `what`: MFG_ERR_INVALID_ARG. */
-enum { MFG_INJECT_NONE = 0, MFG_INJECT_TC_NO_COMMIT = 1 };
+ * context still usable.  MFG_INJECT_BAND_NO_COPY: in the banded substitutions
+ * of a viscosity-field plan's mfg_solve, the copy warp issues neither a
+ * stage's bulk copy nor its expected-bytes arrival, so the stage's bounded
+ * mbarrier wait (4096 polls under this hook) runs out, with the same
+ * outcome.  Either applies to the plan's later mfg_solve calls (no graph
+ * rebuild).  Invalid `what`: MFG_ERR_INVALID_ARG. */
+enum { MFG_INJECT_NONE = 0, MFG_INJECT_TC_NO_COMMIT = 1, MFG_INJECT_BAND_NO_COPY = 2 };
 int mfg_set_fault_injection(mfg_plan_t plan, int what);
 
 /* z = P^{-1} r for the single problem *p, like mfg_apply_precond, but with no

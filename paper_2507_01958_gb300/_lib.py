@@ -20,7 +20,7 @@ MFG_FP64, MFG_MIXED, MFG_MIXED_DF, MFG_MIXED_TC = 0, 1, 2, 3
 MFG_CG_FIXED, MFG_CG_ADAPTIVE = 0, 1
 MFG_LAUNCH_GRAPH, MFG_LAUNCH_EAGER = 0, 1
 MFG_CG_REF_RHS, MFG_CG_REF_RESID = 0, 1
-MFG_INJECT_NONE, MFG_INJECT_TC_NO_COMMIT = 0, 1
+MFG_INJECT_NONE, MFG_INJECT_TC_NO_COMMIT, MFG_INJECT_BAND_NO_COPY = 0, 1, 2
 
 
 class MfgProblem(C.Structure):
@@ -326,7 +326,8 @@ def mfg_get_schedule(plan, b):
 def mfg_set_fault_injection(plan, what):
     """Test hook of the failure-detection paths (see mfg.h): "none" or
     "tc_no_commit", or the integer code."""
-    code = {"none": MFG_INJECT_NONE, "tc_no_commit": MFG_INJECT_TC_NO_COMMIT}.get(what, what)
+    code = {"none": MFG_INJECT_NONE, "tc_no_commit": MFG_INJECT_TC_NO_COMMIT,
+            "band_no_copy": MFG_INJECT_BAND_NO_COPY}.get(what, what)
     _check(LIB.mfg_set_fault_injection(plan.handle, code))
 
 

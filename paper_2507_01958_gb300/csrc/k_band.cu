@@ -363,6 +363,9 @@ __device__ __forceinline__ void bulk_load(void* smem, const void* gmem, uint32_t
       : "memory");
 }
 constexpr uint32_t kBandPolls = 1u << 22;  // mbarrier polls before a wait gives up
+// Poll limit under the fault-injection hook (no copy issued, nothing ever
+// arrives): short, so the test of the timeout path costs milliseconds.
+constexpr uint32_t kBandPollsInjected = 1u << 12;
 // Waits for phase `parity` of the mbarrier, giving up after `polls` polls.
 __device__ __forceinline__ bool band_wait(uint32_t mbar, uint32_t parity, uint32_t polls) {
   for (uint32_t it = 0; it < polls; ++it) {
@@ -494,6 +497,10 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
                                                     DevScalars* sc) {
   constexpr int RG = (kBandRing * G + 3) / 4 * 4;     // right-hand-side stages, 16-byte multiple
   if (sc != nullptr && sc->cg_done) return;
+  // Fault-injection hook (MFG_INJECT_BAND_NO_COPY): no stage copy and no
+  // expected-bytes arrival are issued, so the bounded stage wait must run out.
+  const bool no_copy = sc != nullptr && sc->inject == MFG_INJECT_BAND_NO_COPY;
+  const uint32_t polls = no_copy ? kBandPollsInjected : kBandPolls;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* ring = reinterpret_cast<T*>(smraw);              // kBandRing stages
   T* refill = ring + (size_t)kBandRing * stage;       // kBandRing x G
@@ -515,7 +522,7 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
     if (warp != 2) return;
     if (st < nblk) {
       const int t0 = st * G;
-      if (lane == 0) {
+      if (lane == 0 && !no_copy) {
         const uint32_t mb = smem_addr(&mbar[st % kBandRing]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(sbytes) : "memory");
         bulk_load(ring + (size_t)(st % kBandRing) * stage, Fk + (size_t)st * stage, sbytes, mb);
@@ -546,7 +553,7 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
   int failed = 0;
   for (int st = 0; st < nblk; ++st) {
     bool ok = true;
-    if (warp == 0) ok = band_wait(smem_addr(&mbar[st % kBandRing]), (uint32_t)(st / kBandRing) & 1u, kBandPolls);
+    if (warp == 0) ok = band_wait(smem_addr(&mbar[st % kBandRing]), (uint32_t)(st / kBandRing) & 1u, polls);
     if (warp == 2) cp_async_wait<kBandRing - 3>();
     if (__syncthreads_or(ok ? 0 : 1)) {
       failed = st + 1;
@@ -591,7 +598,7 @@ __global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T*
     const int st = failed - 1;
     if (tid == 0)
       for (int j = st; j < min(nblk, st + kBandRing - 2); ++j)
-        band_wait(smem_addr(&mbar[j % kBandRing]), (uint32_t)(j / kBandRing) & 1u, kBandPolls);
+        band_wait(smem_addr(&mbar[j % kBandRing]), (uint32_t)(j / kBandRing) & 1u, polls);
     for (int t = tid; t < S; t += nth) xk[t] = (T)__int_as_float(0x7fc00000);
     if (tid == 0 && sc != nullptr) {
       sc->status = MFG_ERR_TIMEOUT;

@@ -566,8 +566,9 @@ int mfg_get_schedule(mfg_plan_t pl, int b, mfg_schedule* out) {
 
 int mfg_set_fault_injection(mfg_plan_t pl, int what) {
   if (!pl) return fail(MFG_ERR_INVALID_ARG, "null plan");
-  if (what != MFG_INJECT_NONE && what != MFG_INJECT_TC_NO_COMMIT)
-    return fail(MFG_ERR_INVALID_ARG, "what must be MFG_INJECT_NONE or MFG_INJECT_TC_NO_COMMIT");
+  if (what != MFG_INJECT_NONE && what != MFG_INJECT_TC_NO_COMMIT && what != MFG_INJECT_BAND_NO_COPY)
+    return fail(MFG_ERR_INVALID_ARG,
+                "what must be MFG_INJECT_NONE, MFG_INJECT_TC_NO_COMMIT or MFG_INJECT_BAND_NO_COPY");
   pl->inject = what;
   return MFG_OK;
 }

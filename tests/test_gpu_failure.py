@@ -5,9 +5,11 @@ fault or hang the GPU:
                          or the CP step norm reports it and the instance stops
                          after the iteration that saw it;
   MFG_ERR_NOT_CONVERGED  max_cg = 1 with an unreachable tolerance;
-  MFG_ERR_TIMEOUT        the fault-injection hook under which the tensor-core
-                         time pass issues no MMA and no commit, so its bounded
-                         mbarrier wait must run out (nothing is ever in flight).
+  MFG_ERR_TIMEOUT        the fault-injection hooks under which the tensor-core
+                         time pass issues no MMA and no commit, or the banded
+                         substitutions of a viscosity-field plan issue no stage
+                         copy, so a bounded mbarrier wait must run out (nothing
+                         is ever in flight).
 
 Each case runs in graph and in eager launch mode, checks the status, the
 iteration counters and that the call returned, and then checks that the same
@@ -138,6 +140,32 @@ def test_tensor_core_wait_times_out(mode):
     assert secs < 30.0
     L.mfg_set_fault_injection(plan, "none")
     _check_healthy(plan, p, inst, mode)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_band_wait_times_out(mode):
+    """Under MFG_INJECT_BAND_NO_COPY the banded substitutions of a
+    viscosity-field plan wait on a stage that is never copied; the bounded
+    wait gives up, the instance reports MFG_ERR_TIMEOUT after its first CP
+    iteration and the call returns; the same plan then solves correctly."""
+    L = lib()
+    inst = mi.small(seed=62, dim=2, nx=12, ny=16, nt=8, bc=("neumann", "periodic"), eps=0.0)
+    p = dict(inst["problem"], max_cp=4, cg_tol=1e-12)
+    p["nu_field"] = mi.viscosity_field(p, p["nu"], 10.0, 162, "smooth")
+    plan = L.mfg_plan(p, precision="mixed_tc")
+    L.mfg_set_fault_injection(plan, "band_no_copy")
+    plan, rc, st, y, secs = _run(p, inst, mode=mode, plan=plan)
+    assert rc == L.MFG_ERR_TIMEOUT and st.status == L.MFG_ERR_TIMEOUT
+    assert st.cp_iters == 1 and st.cg_iters == 0
+    assert secs < 30.0
+    L.mfg_set_fault_injection(plan, "none")
+    _, rc, st, y, _ = _run(p, inst, mode=mode, plan=plan)
+    assert rc == L.MFG_OK and st.status == L.MFG_OK and st.cp_iters == p["max_cp"]
+    ref = Solver(p, inst["m0"], inst["V"], inst["W"], method="lu").run(inst["y0"], iters=p["max_cp"])
+    # the bound of the constant-nu iterates, max(1e-8, 10 kappa u), with
+    # kappa = cond(AAt) for K_nu by dense eigenvalues (a 12 x 16 x 8 grid)
+    ev = np.linalg.eigvalsh(ops.AAt(p).toarray())
+    assert rel(y, ref["y"]) <= max(1e-8, 10.0 * ev[-1] / ev[0] * 2.0 ** -53)
 
 
 def test_fault_injection_rejects_unknown_codes():
