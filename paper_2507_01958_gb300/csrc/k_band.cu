@@ -492,7 +492,7 @@ __device__ __forceinline__ T row_dot(const T* sec, int r, const T (&xr)[G]) {
 // bounded: a stage that never arrives marks this frequency's output NaN,
 // records MFG_ERR_TIMEOUT and ends the kernel.
 template <typename T, bool BWD, int G>
-__global__ void __launch_bounds__(512) k_band_pass(const T* __restrict__ rhs, T* __restrict__ sol,
+__global__ void __launch_bounds__(512, 1) k_band_pass(const T* __restrict__ rhs, T* __restrict__ sol,
                                                     const T* __restrict__ F, int S, int w, int stage,
                                                     DevScalars* sc) {
   constexpr int RG = (kBandRing * G + 3) / 4 * 4;     // right-hand-side stages, 16-byte multiple
