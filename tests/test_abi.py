@@ -87,6 +87,16 @@ def test_plan_rejects_invalid_viscosity_fields_without_gpu():
         assert text in L.mfg_last_error()
 
 
+def test_fault_injection_codes_match_header():
+    """The binding's fault-injection names map to the header's enum values."""
+    L = _lib()
+    txt = open(HEADER).read()
+    enum = dict((k, int(v)) for k, v in re.findall(r"(MFG_INJECT_\w+)\s*=\s*(\d+)", txt))
+    assert enum == {"MFG_INJECT_NONE": 0, "MFG_INJECT_TC_NO_COMMIT": 1, "MFG_INJECT_BAND_NO_COPY": 2}
+    for key, val in enum.items():
+        assert getattr(L, key) == val
+
+
 def test_precision_codes_match_header():
     """The binding's precision names map to the header's enum values, and an
     unknown code is rejected on the host."""
